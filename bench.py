@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU threshold (T-overlap) query.
+
+Workload (the many-criteria configuration): 64 bitmaps over r = 2^26 rows,
+densities log-uniform in [1e-4, 0.3], bitmaps 0-31 i.i.d. Bernoulli and
+32-63 clustered (runs of mean 256 rows), encoded in the library's 64-bit
+word-aligned run-length format (~125 MiB of compressed input).  One step runs
+the four queries over all 64 bitmaps at T = 2, 16, 32 and 63.
+
+Reported (one JSON line from rank 0):
+  value         queries/s over the timed steps, index resident in HBM, output
+                into a device buffer; L2 is flushed (256 MiB write, untimed)
+                before every query, each query timed with CUDA events
+  input_gbs     compressed input bytes / time (Sec. 7 of the paper measures
+                throughput as input bytes over time)
+  e2e           the same queries through the C ABI with host ids and a host
+                output buffer (the result copied back inside the timed call)
+  roofline      the query kernel: algorithmic bytes (compressed input read +
+                compressed output written) per launch / its event-timed
+                duration, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle on the same queries (bounded sample)
+
+Multi-GPU (torchrun): every rank holds a full replica and runs the same
+steps; value = all ranks' queries / the slowest rank's time ("weak").
+
+--impl reference times the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = ("threshold queries/s and compressed-input GB/s (bit-exact) vs HBM peak; "
+          "batched+learned vs plain")
+WORKLOAD = ("many-criteria: 64 bitmaps x 2^26 rows, densities log-uniform [1e-4, 0.3], "
+            "half i.i.d., half clustered (mean run 256 rows); one step = T in {2,16,32,63}")
+KERNEL_SOURCES = ("thr_device.cuh", "thr_query_kernel.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1402_4466_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "threshold_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.lines = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_index_inputs(seed):
+    import paper_1402_4466_gb300 as thr
+    r = synth.MANY_R
+    words, dens = synth.many_criteria(seed, synth.MANY_N, r,
+                                      workers=min(16, os.cpu_count() or 1))
+    gw, goff = thr.encode_many(words, r)
+    return r, gw, goff
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1402_4466_gb300 as thr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.Stream()
+    r, gw, goff = make_index_inputs(args.seed)
+    t0 = time.perf_counter()
+    idx = thr.idx_build_rle(gw, goff, r, stream=stream)
+    build_s = time.perf_counter() - t0
+    ids = np.arange(synth.MANY_N, dtype=np.uint32)
+    Ts = list(synth.MANY_TS)
+    in_bytes = 8 * int(goff[-1])  # every query reads all 64 streams
+    W = idx.nwords
+    dout = torch.empty(W + 1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    out_words = {}
+
+    def one_query(T, timed):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # write 256 MiB > L2 before every query (untimed)
+        stream.synchronize()
+        ev0.record(stream)
+        n = thr.thr_query(idx, ids, T, out=dout, flags=thr.THR_PROFILE, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        out_words[T] = n
+        return ev0.elapsed_time(ev1), thr.thr_last_kernel_ms()
+
+    for _ in range(args.warmup):
+        for T in Ts:
+            one_query(T, False)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    q_ms, k_ms, k_bytes = [], [], []
+    for _ in range(args.steps):
+        for T in Ts:
+            qm, km = one_query(T, True)
+            q_ms.append(qm)
+            k_ms.append(km)
+            k_bytes.append(in_bytes + 8 * out_words[T])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(q_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    nq = len(q_ms) * world
+    value = nq / (total_ms / 1e3)
+    input_gbs = (in_bytes * nq) / (total_ms / 1e3) / 1e9
+
+    # end to end through the C ABI: host ids in, host result out
+    e2e_ms, d2h = [], 0
+    for _ in range(args.steps):
+        for T in Ts:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            t1 = time.perf_counter()
+            res = thr.thr_query(idx, ids, T, stream=stream)
+            e2e_ms.append((time.perf_counter() - t1) * 1e3)
+            d2h += 8 * len(res) + 16
+    e2e_value = len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    avg_bytes = statistics.mean(k_bytes)
+    avg_kms = statistics.mean(k_ms)
+    achieved = avg_bytes / (avg_kms / 1e3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "input_gbs": round(input_gbs, 2),
+        "config": {
+            "workload": WORKLOAD,
+            "bitmaps": synth.MANY_N,
+            "rows": r,
+            "thresholds": Ts,
+            "compressed_input_bytes_per_query": in_bytes,
+            "output_words": {str(k): int(v) for k, v in out_words.items()},
+            "l2": "flushed before every query (256 MiB device write, untimed)",
+            "parallelism": f"replicas x{world}",
+            "index_build_s": round(build_s, 3),
+        },
+        "e2e": {"value": round(e2e_value, 3), "unit": "queries/s",
+                "h2d_bytes_per_step": 4 * len(ids) * len(Ts),
+                "d2h_bytes_per_step": d2h // max(args.steps, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": ncu_traffic(), "peak_kind": peak_kind,
+                     "kernel": "k_threshold", "bytes_per_launch": int(avg_bytes),
+                     "kernel_ms": round(avg_kms, 5)},
+        "gpu_launches": len(q_ms),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(gw, goff, r, ids, Ts, idx, thr)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(gw, goff, r, ids, Ts, idx, thr):
+    """The oracle (plain single-threaded ScanCount) on the step's 4 queries,
+    once each; also checks the GPU results against it."""
+    import oracle
+    streams = [gw[int(goff[i]): int(goff[i + 1])] for i in range(len(goff) - 1)]
+    o = oracle.Index(streams, r)
+    t = 0.0
+    exact = True
+    for T in Ts:
+        t0 = time.perf_counter()
+        want = o.threshold(ids, T)
+        t += time.perf_counter() - t0
+        exact &= bool(np.array_equal(thr.thr_query(idx, ids, T), want))
+    return {"value": round(len(Ts) / t, 4), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": "the 4 queries of one step (T = 2, 16, 32, 63), once each, one thread",
+            "gpu_matches_oracle": exact}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step runs the four queries
+    of a step concurrently on four host threads (ctypes releases the GIL)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import paper_1402_4466_gb300 as thr  # host codec only (encoding the inputs)
+    del thr
+    r = synth.MANY_R
+    words, _ = synth.many_criteria(args.seed, synth.MANY_N, r,
+                                   workers=min(16, os.cpu_count() or 1))
+    streams = [oracle.encode(w, r) for w in words]
+    o = oracle.Index(streams, r)
+    ids = np.arange(synth.MANY_N, dtype=np.uint32)
+    Ts = list(synth.MANY_TS)
+
+    def step():
+        th = [threading.Thread(target=o.threshold, args=(ids, T)) for T in Ts]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = len(Ts) * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bitmaps": synth.MANY_N, "rows": r, "thresholds": Ts},
+        "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": len(Ts),
+                         "kind": "oracle",
+                         "sample": "every step: the 4 queries, one per host thread"},
+        "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

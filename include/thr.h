@@ -1,0 +1,167 @@
+/*
+ * thr.h -- C ABI of libthr, a GPU (sm_103a) implementation of the threshold
+ * (T-overlap) query over run-length-compressed bitmaps described by Kaser &
+ * Lemire, "Compressed bitmap indexes: beyond unions and intersections"
+ * (arXiv 1402.4466).
+ *
+ * The query (Sec. 2, "Formulation"): given N bitmaps over the rows [0, r) and
+ * a threshold T, return the rows that are set in at least T of the N inputs.
+ * T = 1 is a union and T = N an intersection; a bitmap listed twice counts
+ * twice; T = 0 returns every row and T > N returns no row.
+ *
+ * Stream format.  Every bitmap and every result is a stream of 64-bit words
+ * in a word-aligned run-length format in the style of EWAH (Sec. 3.1,
+ * "Compressed Bitmaps": marker words carry the length of a run of fill words
+ * and the number of dirty words that follow; 64-bit EWAH uses a 32-bit fill
+ * counter).  The paper defers the exact layout to earlier work; this library
+ * fixes it as:
+ *   marker word   bit 0       fill bit b (fill words are 0 or ~0)
+ *                 bits 1..32  F, number of fill words
+ *                 bits 33..63 L, number of literal ("dirty") words after it
+ *   stream        [marker, L literals] groups covering exactly
+ *                 W = ceil(r/64) uncompressed words; uncompressed word i holds
+ *                 rows 64i..64i+63, least-significant bit = smallest row.
+ *   canonical     (i) no literal equals 0 or ~0; (ii) fill runs are maximal;
+ *                 (iii) a marker starts only where a fill follows a literal,
+ *                 the fill value changes, or a counter overflows; (iv) F = 0
+ *                 implies b = 0; (v) bits >= r of the last word are 0, so a
+ *                 ragged last word whose valid bits are all 1 is a literal;
+ *                 (vi) F = 0 only in the first marker or after a marker whose
+ *                 literal count overflowed.  Hence a stream has at most W + 1
+ *                 words.  Inputs must be canonical; outputs always are.
+ *
+ * Limits: 1 <= r and W = ceil(r/64) <= 2^31 - 2 (so no counter overflows and
+ * word indices fit 31 bits); 1 <= n <= 65536 bitmaps per query.
+ *
+ * Errors: every call returns a thr_status; no C++ exception crosses the ABI.
+ * thr_last_error() describes the last failure of the calling thread.
+ * A CUDA failure returns THR_E_CUDA; a device-side wait that exceeded its
+ * iteration limit returns THR_E_TIMEOUT (the result is then undefined, the
+ * CUDA context stays usable).
+ */
+#ifndef THR_H
+#define THR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct thr_index thr_index; /* opaque; owns all device memory */
+
+typedef enum {
+    THR_OK = 0,
+    THR_E_INVAL = 1,   /* bad argument (null pointer, id out of range, n = 0) */
+    THR_E_FORMAT = 2,  /* an input stream is not canonical for r rows */
+    THR_E_NOMEM = 3,   /* host or device allocation failed */
+    THR_E_NOSPACE = 4, /* output buffer too small; required size returned */
+    THR_E_CUDA = 5,    /* a CUDA runtime call failed */
+    THR_E_TIMEOUT = 6  /* a device wait hit its iteration limit */
+} thr_status;
+
+/* flags for thr_query / thr_query_batch */
+#define THR_OUT_DEVICE 0x1u     /* out / pool are device pointers */
+#define THR_POLICY_PLAIN 0x00u  /* batch: one launch per query, fixed variant */
+#define THR_POLICY_RULE 0x10u   /* batch: rule-based variant choice */
+#define THR_POLICY_LEARNED 0x20u /* batch: learned cost-model choice */
+#define THR_POLICY_MASK 0xF0u
+#define THR_PROFILE 0x100u      /* time the query kernel with CUDA events */
+
+/*
+ * Build a device-resident index from canonical streams (Sec. 3.1 format
+ * above; Sec. 2: the N sets share the universe [0, r)).
+ *   words     host array: all streams concatenated
+ *   offsets   host array of nbitmaps + 1 word offsets; stream i is
+ *             words[offsets[i] .. offsets[i+1])
+ *   nbitmaps  >= 1
+ *   r         number of rows of every bitmap
+ *   cuda_stream  cudaStream_t used for the uploads and build kernels (0 ok)
+ *   out       receives the new index on THR_OK, untouched otherwise
+ * The input is copied; the caller keeps ownership of words and offsets.
+ * Every stream is validated on the host: one that is not canonical for r
+ * rows returns THR_E_FORMAT.  The index lives on the device that is current
+ * at the call; queries must run with that device current.  Returns after the
+ * build work on cuda_stream has completed.
+ */
+thr_status idx_build_rle(const uint64_t *words, const uint64_t *offsets,
+                         uint32_t nbitmaps, uint64_t r, void *cuda_stream,
+                         thr_index **out);
+
+/*
+ * Threshold query (Sec. 2): the rows set in at least T of the bitmaps
+ * ids[0..n), encoded canonically.
+ *   idx       index from idx_build_rle
+ *   ids       host array of n bitmap ids (< nbitmaps; duplicates count with
+ *             multiplicity)
+ *   n         1 <= n <= 65536
+ *   T         any value; 0 gives every row, > n gives none
+ *   out       caller-owned buffer of cap words: host memory, or device memory
+ *             when flags has THR_OUT_DEVICE
+ *   cap       capacity of out in words; cap >= ceil(r/64) + 1 always suffices
+ *   out_len   receives the encoded length in words.  When it exceeds cap the
+ *             call returns THR_E_NOSPACE and the contents of out are
+ *             unspecified (at most cap words are written).
+ *   flags     THR_OUT_DEVICE or 0
+ *   cuda_stream  cudaStream_t for all work (0 ok)
+ * On return the result and *out_len are complete (the call synchronises
+ * cuda_stream).  Concurrent queries on one index are allowed.
+ */
+thr_status thr_query(const thr_index *idx, const uint32_t *ids, uint32_t n,
+                     uint32_t T, uint64_t *out, uint64_t cap,
+                     uint64_t *out_len, uint32_t flags, void *cuda_stream);
+
+/*
+ * Batch of nq threshold queries (Sec. 2) over one index.
+ *   id_off    host array of nq + 1 offsets into ids; query q uses
+ *             ids[id_off[q] .. id_off[q+1])
+ *   ids, T    host arrays (T has nq entries)
+ *   pool      caller-owned output pool of pool_cap words (host, or device
+ *             with THR_OUT_DEVICE); query q's result is stored at
+ *             pool[out_off[q] .. out_off[q] + out_len[q])
+ *   out_off, out_len  host arrays of nq entries, filled on return
+ *   flags     THR_OUT_DEVICE | one THR_POLICY_* value
+ * pool_cap >= nq * (ceil(r/64) + 1) never yields THR_E_NOSPACE; a smaller
+ * pool works when the results fit, else THR_E_NOSPACE with out_len holding
+ * every query's length.  Results are identical to nq calls of thr_query.
+ */
+thr_status thr_query_batch(const thr_index *idx, uint32_t nq,
+                           const uint32_t *id_off, const uint32_t *ids,
+                           const uint32_t *T, uint64_t *pool,
+                           uint64_t pool_cap, uint64_t *out_off,
+                           uint64_t *out_len, uint32_t flags,
+                           void *cuda_stream);
+
+/* Release an index (NULL-safe); waits for in-flight work on its device. */
+void idx_free(thr_index *idx);
+
+/* Number of bitmaps, rows and total stored words of an index. */
+thr_status idx_info(const thr_index *idx, uint32_t *nbitmaps, uint64_t *r,
+                    uint64_t *total_words);
+
+/*
+ * Host codec.  thr_rle_encode writes the canonical stream of the
+ * uncompressed bitmap words[0..nwords) (nwords = ceil(r/64), bits >= r must
+ * be 0) into out (cap words), *out_len = its length (THR_E_NOSPACE if it
+ * exceeds cap).  thr_rle_validate returns THR_OK for a canonical stream of an
+ * r-row bitmap and THR_E_FORMAT otherwise.  Both are host-only.
+ */
+thr_status thr_rle_encode(const uint64_t *words, uint64_t nwords, uint64_t r,
+                          uint64_t *out, uint64_t cap, uint64_t *out_len);
+thr_status thr_rle_validate(const uint64_t *stream, uint64_t len, uint64_t r);
+
+/*
+ * Device time in milliseconds of the query kernel of the last thr_query
+ * call on this thread that passed THR_PROFILE (CUDA events recorded on the
+ * query's stream right before and after the kernel launch); -1 if none.
+ */
+double thr_last_kernel_ms(void);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *thr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THR_H */

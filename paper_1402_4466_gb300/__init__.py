@@ -1,0 +1,252 @@
+"""Python binding of libthr: GPU threshold (T-overlap) queries over
+run-length-compressed bitmaps (Kaser & Lemire, arXiv 1402.4466).
+
+Argument marshalling only: every step of a query runs in the CUDA kernels of
+``csrc/`` behind the C ABI of ``include/thr.h``.  The functions keep the ABI's
+names.  There is no CPU fallback: if the library cannot be built or loaded,
+``load()`` raises.
+
+Arrays are numpy (host) or objects with ``data_ptr()`` and ``is_cuda``
+(torch tensors, for device outputs); PyTorch is only used by callers for
+device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+THR_OK, THR_E_INVAL, THR_E_FORMAT, THR_E_NOMEM = 0, 1, 2, 3
+THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT = 4, 5, 6
+THR_OUT_DEVICE = 0x1
+THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
+THR_PROFILE = 0x100
+
+STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
+                3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",
+                6: "THR_E_TIMEOUT"}
+
+# every symbol include/thr.h declares
+ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "idx_free",
+               "idx_info", "thr_rle_encode", "thr_rle_validate",
+               "thr_last_kernel_ms", "thr_last_error")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ThrError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (when missing or stale) and load libthr.so; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            u64, u32 = ctypes.c_uint64, ctypes.c_uint32
+            vp, u64p, u32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)
+            lib.idx_build_rle.argtypes = [vp, vp, u32, u64, vp, ctypes.POINTER(vp)]
+            lib.thr_query.argtypes = [vp, vp, u32, u32, vp, u64, u64p, u32, vp]
+            lib.thr_query_batch.argtypes = [vp, u32, vp, vp, vp, vp, u64, vp, vp, u32, vp]
+            lib.idx_free.argtypes = [vp]
+            lib.idx_free.restype = None
+            lib.idx_info.argtypes = [vp, u32p, u64p, u64p]
+            lib.thr_rle_encode.argtypes = [vp, u64, u64, vp, u64, u64p]
+            lib.thr_rle_validate.argtypes = [vp, u64, u64]
+            lib.thr_last_error.argtypes = []
+            lib.thr_last_error.restype = ctypes.c_char_p
+            lib.thr_last_kernel_ms.argtypes = []
+            lib.thr_last_kernel_ms.restype = ctypes.c_double
+            for f in ("idx_build_rle", "thr_query", "thr_query_batch", "idx_info",
+                      "thr_rle_encode", "thr_rle_validate"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def thr_last_error() -> str:
+    return load().thr_last_error().decode()
+
+
+def thr_last_kernel_ms() -> float:
+    return float(load().thr_last_kernel_ms())
+
+
+def _check(st: int, where: str):
+    if st != THR_OK:
+        raise ThrError(st, where, thr_last_error())
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+class Index:
+    """Handle of a device-resident index (idx_free on close / deletion)."""
+
+    def __init__(self, handle: int, nbitmaps: int, r: int):
+        self.handle = handle
+        self.nbitmaps = nbitmaps
+        self.r = r
+        self.nwords = (r + 63) // 64
+
+    def close(self):
+        if self.handle:
+            load().idx_free(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n = ctypes.c_uint32(0)
+        r = ctypes.c_uint64(0)
+        t = ctypes.c_uint64(0)
+        _check(load().idx_info(ctypes.c_void_p(self.handle), ctypes.byref(n),
+                               ctypes.byref(r), ctypes.byref(t)), "idx_info")
+        return {"nbitmaps": n.value, "r": r.value, "total_words": t.value}
+
+
+def idx_build_rle(words, offsets, r: int, stream=None) -> Index:
+    """Device index from canonical streams concatenated in `words`, stream i
+    being words[offsets[i]:offsets[i+1]]."""
+    lib = load()
+    w = _u64(words)
+    o = _u64(offsets)
+    h = ctypes.c_void_p(0)
+    _check(lib.idx_build_rle(ctypes.c_void_p(w.ctypes.data if w.size else 0),
+                             ctypes.c_void_p(o.ctypes.data), len(o) - 1, int(r),
+                             ctypes.c_void_p(_stream(stream)), ctypes.byref(h)),
+           "idx_build_rle")
+    return Index(h.value, len(o) - 1, int(r))
+
+
+def idx_free(idx: Index):
+    idx.close()
+
+
+def thr_query(idx: Index, ids, T: int, out=None, flags: int = 0, stream=None,
+              cap: int | None = None):
+    """Threshold query.  With out=None returns the result stream as a numpy
+    array; with a device tensor `out` (THR_OUT_DEVICE is added) or a host
+    array, fills it and returns the number of words written."""
+    lib = load()
+    ids = _u32(ids)
+    n = ctypes.c_uint64(0)
+    if out is None:
+        buf = np.empty(idx.nwords + 1, dtype=np.uint64)
+        _check(lib.thr_query(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                             ids.size, int(T), ctypes.c_void_p(buf.ctypes.data), buf.size,
+                             ctypes.byref(n), int(flags), ctypes.c_void_p(_stream(stream))),
+               "thr_query")
+        return buf[: n.value].copy()
+    if getattr(out, "is_cuda", False):
+        flags |= THR_OUT_DEVICE
+    size = cap if cap is not None else (out.numel() if hasattr(out, "numel") else out.size)
+    st = lib.thr_query(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data), ids.size,
+                       int(T), ctypes.c_void_p(_ptr(out)), int(size), ctypes.byref(n),
+                       int(flags), ctypes.c_void_p(_stream(stream)))
+    if st == THR_E_NOSPACE:
+        raise ThrError(st, "thr_query", f"needs {n.value} words")
+    _check(st, "thr_query")
+    return n.value
+
+
+def thr_query_raw(idx: Index, ids, T: int, out_ptr: int, cap: int, flags: int,
+                  stream=None) -> tuple[int, int]:
+    """ABI call with a raw output pointer; returns (status, out_len)."""
+    ids = _u32(ids)
+    n = ctypes.c_uint64(0)
+    st = load().thr_query(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                          ids.size, int(T), ctypes.c_void_p(out_ptr), int(cap),
+                          ctypes.byref(n), int(flags), ctypes.c_void_p(_stream(stream)))
+    return st, n.value
+
+
+def thr_query_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None):
+    """Batch of (ids, T) queries.  Returns (out_off, out_len, pool); with
+    pool=None a host pool of the worst-case size is allocated."""
+    lib = load()
+    nq = len(queries)
+    id_off = np.zeros(nq + 1, dtype=np.uint32)
+    id_off[1:] = np.cumsum([len(q[0]) for q in queries])
+    ids = _u32(np.concatenate([_u32(q[0]) for q in queries]) if nq else [])
+    T = _u32([q[1] for q in queries])
+    if pool is None:
+        pool = np.empty(max(nq * (idx.nwords + 1), 1), dtype=np.uint64)
+    if getattr(pool, "is_cuda", False):
+        flags |= THR_OUT_DEVICE
+    size = pool.numel() if hasattr(pool, "numel") else pool.size
+    out_off = np.zeros(nq, dtype=np.uint64)
+    out_len = np.zeros(nq, dtype=np.uint64)
+    _check(lib.thr_query_batch(ctypes.c_void_p(idx.handle), nq,
+                               ctypes.c_void_p(id_off.ctypes.data),
+                               ctypes.c_void_p(ids.ctypes.data if ids.size else 0),
+                               ctypes.c_void_p(T.ctypes.data), ctypes.c_void_p(_ptr(pool)),
+                               int(size), ctypes.c_void_p(out_off.ctypes.data),
+                               ctypes.c_void_p(out_len.ctypes.data), int(flags),
+                               ctypes.c_void_p(_stream(stream))), "thr_query_batch")
+    return out_off, out_len, pool
+
+
+def thr_rle_encode(words, r: int) -> np.ndarray:
+    """Canonical stream of uncompressed words (host codec of the library)."""
+    lib = load()
+    w = _u64(words)
+    cap = w.size + 1
+    out = np.empty(cap, dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(lib.thr_rle_encode(ctypes.c_void_p(w.ctypes.data if w.size else 0), w.size, int(r),
+                              ctypes.c_void_p(out.ctypes.data), cap, ctypes.byref(n)),
+           "thr_rle_encode")
+    return out[: n.value].copy()
+
+
+def thr_rle_validate(stream, r: int) -> int:
+    s = _u64(stream)
+    return int(load().thr_rle_validate(ctypes.c_void_p(s.ctypes.data if s.size else 0),
+                                       s.size, int(r)))
+
+
+def encode_many(word_arrays, r: int):
+    """Encode several uncompressed bitmaps; returns (concatenated words,
+    offsets) ready for idx_build_rle."""
+    streams = [thr_rle_encode(w, r) for w in word_arrays]
+    offs = np.zeros(len(streams) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(s) for s in streams])
+    return (np.concatenate(streams) if streams else np.zeros(0, np.uint64)), offs

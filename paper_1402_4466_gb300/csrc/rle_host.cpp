@@ -1,0 +1,142 @@
+// Host codec of the stream format (see rle_host.h and include/thr.h).
+#include "rle_host.h"
+
+#include <cstdio>
+
+namespace thr {
+
+namespace {
+
+inline bool is_fill_word(uint64_t v) { return v == 0 || v == ~0ull; }
+
+struct Emitter {
+    uint64_t* out;
+    uint64_t cap;
+    uint64_t n = 0;
+    void put(uint64_t v) {
+        if (n < cap && out) out[n] = v;
+        ++n;
+    }
+};
+
+}  // namespace
+
+int scan_stream(const uint64_t* s, uint64_t len, uint64_t r, StreamScan* scan,
+                std::string* why) {
+    auto fail = [&](const char* msg, uint64_t at) {
+        if (why) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "%s (stream word %llu)", msg,
+                          (unsigned long long)at);
+            *why = buf;
+        }
+        return 2;
+    };
+    const uint64_t W = (r + 63) / 64;
+    const unsigned ragged = unsigned(r % 64);
+    scan->marker_pos.clear();
+    scan->set_rows = scan->literal_words = scan->ones_fill_words = 0;
+    if (W == 0) {
+        if (len != 1 || s[0] != 0) return fail("r = 0 requires the stream [0]", 0);
+        scan->marker_pos.push_back(0);
+        return 0;
+    }
+    if (len > kMaxWords + 1) return fail("stream longer than W + 1 words", 0);
+    uint64_t at = 0, done = 0;  // stream cursor, uncompressed words covered
+    bool have_prev = false;
+    uint64_t pF = 0, pL = 0, pb = 0;
+    while (done < W) {
+        if (at >= len) return fail("stream ends before covering ceil(r/64) words", at);
+        const uint64_t m = s[at];
+        const uint64_t b = marker_fill_bit(m), F = marker_fill_len(m),
+                       L = marker_lit_count(m);
+        if (F == 0 && L == 0) return fail("marker covers no word", at);
+        if (F == 0 && b) return fail("fill bit set on an empty fill", at);
+        if (have_prev) {
+            if (F == 0 && pL != kLitMax)
+                return fail("marker without fill after an unsaturated literal run", at);
+            if (F > 0 && pL == 0 && pb == b && pF != kFillMax)
+                return fail("fill run split over two markers", at);
+        }
+        if (F > W - done || L > W - done - F) return fail("marker runs past the last word", at);
+        if (b && ragged && done + F == W) return fail("fill of ones over the ragged last word", at);
+        scan->marker_pos.push_back(uint32_t(at));
+        if (b) {
+            scan->set_rows += 64 * F;
+            scan->ones_fill_words += F;
+        }
+        done += F;
+        ++at;
+        if (L > len - at) return fail("literal run truncated", at);
+        for (uint64_t k = 0; k < L; ++k) {
+            const uint64_t v = s[at + k];
+            if (is_fill_word(v)) return fail("literal word equal to a fill word", at + k);
+            if (ragged && done + k == W - 1 && (v >> ragged) != 0)
+                return fail("bits past r in the last word", at + k);
+            scan->set_rows += uint64_t(__builtin_popcountll(v));
+        }
+        at += L;
+        done += L;
+        scan->literal_words += L;
+        pF = F;
+        pL = L;
+        pb = b;
+        have_prev = true;
+    }
+    if (at != len) return fail("words after the last group", at);
+    return 0;
+}
+
+int encode_words(const uint64_t* words, uint64_t nwords, uint64_t r,
+                 uint64_t* out, uint64_t cap, uint64_t* out_len) {
+    const uint64_t W = (r + 63) / 64;
+    if (nwords != W || !out_len || (W > 0 && !words)) return 1;
+    if (W > kMaxWords) return 1;
+    if ((r % 64) && (words[W - 1] >> (r % 64)) != 0) return 1;
+    Emitter e{out, cap};
+    if (W == 0) {
+        e.put(0);
+        *out_len = e.n;
+        return e.n <= cap ? 0 : 4;
+    }
+    // One pending group [fill run][literal run]; it is emitted when a fill
+    // word follows literals, when the fill value changes, or on overflow.
+    bool open = false;
+    uint64_t gb = 0, gF = 0, gL = 0, gfirst = 0;
+    auto flush = [&]() {
+        if (!open) return;
+        e.put(marker_word(gF ? gb : 0, gF, gL));
+        for (uint64_t k = 0; k < gL; ++k) e.put(words[gfirst + k]);
+        open = false;
+    };
+    for (uint64_t i = 0; i < W; ++i) {
+        const uint64_t v = words[i];
+        if (is_fill_word(v)) {
+            const uint64_t fb = v ? 1 : 0;
+            if (open && gL == 0 && gb == fb && gF < kFillMax) {
+                ++gF;
+            } else {
+                flush();
+                open = true;
+                gb = fb;
+                gF = 1;
+                gL = 0;
+            }
+        } else {
+            if (open && gL == kLitMax) flush();
+            if (!open) {
+                open = true;
+                gb = 0;
+                gF = 0;
+                gL = 0;
+            }
+            if (gL == 0) gfirst = i;
+            ++gL;
+        }
+    }
+    flush();
+    *out_len = e.n;
+    return e.n <= cap ? 0 : 4;
+}
+
+}  // namespace thr

@@ -1,0 +1,459 @@
+// C ABI of libthr (include/thr.h): index build, threshold queries, batches.
+//
+// Host responsibilities: argument checks, stream validation (the format's
+// marker chain is sequential, so the validating walk that also records every
+// marker position runs on the host, one thread per group of bitmaps),
+// uploads, scratch allocation (stream-ordered), kernel choice and the final
+// device->host read of the result length.  Every step of the query itself
+// runs in the kernels of thr_device.cuh / thr_query_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/thr.h"
+#include "rle_host.h"
+#include "thr_device.cuh"
+#include "thr_launch.h"
+
+using namespace thr;
+
+struct thr_index {
+    int device = 0;
+    uint32_t nbitmaps = 0;
+    uint64_t r = 0;
+    uint32_t W = 0;   // ceil(r / 64)
+    uint32_t NG = 0;  // ceil(W / 128)
+    uint64_t total_words = 0;
+    uint64_t total_markers = 0;
+    uint64_t* d_words = nullptr;
+    uint2* d_mtab = nullptr;
+    uint32_t* d_ttab = nullptr;
+    BitmapDesc* d_desc = nullptr;
+    std::vector<BitmapDesc> desc;
+    std::vector<uint64_t> set_rows;
+    int num_sms = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+thread_local double g_kernel_ms = -1.0;
+
+thr_status fail(thr_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+thr_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(THR_E_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(THR_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Pinned per-thread buffer for the few words read back after a query.
+struct PinnedCtl {
+    uint32_t* p = nullptr;
+    ~PinnedCtl() {
+        if (p) cudaFreeHost(p);
+    }
+};
+thread_local PinnedCtl g_ctl;
+
+cudaError_t pinned_ctl(uint32_t** out) {
+    if (!g_ctl.p) {
+        cudaError_t e = cudaMallocHost(&g_ctl.p, 64);
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_ctl.p;
+    return cudaSuccess;
+}
+
+int bit_length(uint64_t v) {
+    int n = 0;
+    while (v) {
+        ++n;
+        v >>= 1;
+    }
+    return n;
+}
+
+// RAII for stream-ordered scratch.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    cudaError_t alloc(void** p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+struct WidthChoice {
+    const KernelEntry* k;
+    uint32_t zmode;
+};
+
+WidthChoice choose_width(uint32_t n, uint32_t T) {
+    int cnt = 0;
+    const KernelEntry* tab = kernel_table(&cnt);
+    // Counting ones needs 2^S > T; counting the zeros of the active inputs
+    // needs 2^S > n - T + 1.  T = 0 and T > n never reach the counters.
+    uint32_t zmode = 0;
+    int need = 1;
+    if (T >= 1 && T <= n) {
+        const int s1 = bit_length(T), s0 = bit_length(uint64_t(n) - T + 1);
+        zmode = s0 < s1 ? 1u : 0u;
+        need = std::min(s1, s0);
+    }
+    for (int i = 0; i < cnt; ++i)
+        if (tab[i].S >= need) return {&tab[i], zmode};
+    return {&tab[cnt - 1], zmode};
+}
+
+// One query, output to a device buffer `dout` of `cap` words.  Returns the
+// encoded length in *len (also when it exceeds cap).
+thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
+                     uint32_t T, uint64_t* dout, uint64_t cap, uint64_t* len,
+                     cudaStream_t st, bool profile) {
+    const uint32_t ntiles = (idx->W + kTW - 1) / kTW;
+    Scratch scr(st);
+    uint32_t* d_ids = nullptr;
+    uint32_t* d_states = nullptr;
+    uint32_t* d_ctl = nullptr;
+    CK(scr.alloc((void**)&d_ids, sizeof(uint32_t) * n), "scratch (ids)");
+    CK(scr.alloc((void**)&d_states, sizeof(uint32_t) * kStateWords * ntiles),
+       "scratch (tile states)");
+    CK(scr.alloc((void**)&d_ctl, 64), "scratch (control)");
+    CK(cudaMemcpyAsync(d_ids, ids, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st),
+       "upload ids");
+    CK(cudaMemsetAsync(d_states, 0, sizeof(uint32_t) * kStateWords * ntiles, st),
+       "clear tile states");
+    CK(cudaMemsetAsync(d_ctl, 0, 64, st), "clear control words");
+
+    const WidthChoice wc = choose_width(n, T);
+    QueryParams p{};
+    p.words = idx->d_words;
+    p.mtab = idx->d_mtab;
+    p.ttab = idx->d_ttab;
+    p.desc = idx->d_desc;
+    p.ids = d_ids;
+    p.n = n;
+    p.T = T;
+    p.zmode = wc.zmode;
+    p.W = idx->W;
+    p.NG = idx->NG;
+    p.ntiles = ntiles;
+    p.ragged = uint32_t(idx->r % 64);
+    p.spin_limit = 1u << 20;
+    p.out = dout;
+    p.cap = cap;
+    p.states = d_states;
+    p.ctl = d_ctl;
+    int per_sm = 0;
+    CK(wc.k->occupancy(&per_sm), "occupancy query");
+    const int grid = int(std::min<uint64_t>(ntiles, uint64_t(std::max(per_sm, 1)) * idx->num_sms));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (profile) {
+        CK(cudaEventCreate(&ev[0]), "event");
+        CK(cudaEventCreate(&ev[1]), "event");
+        CK(cudaEventRecord(ev[0], st), "event record");
+    }
+    CK(wc.k->launch(p, std::max(grid, 1), st), "launch threshold kernel");
+    if (profile) CK(cudaEventRecord(ev[1], st), "event record");
+
+    uint32_t* h = nullptr;
+    CK(pinned_ctl(&h), "pinned buffer");
+    CK(cudaMemcpyAsync(h, d_ctl, 16, cudaMemcpyDeviceToHost, st), "read result length");
+    CK(cudaStreamSynchronize(st), "query");
+    if (profile) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+        g_kernel_ms = ms;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    if (h[1] & kErrSpin)
+        return fail(THR_E_TIMEOUT, "tile look-back exceeded its spin limit");
+    *len = uint64_t(h[2]) | (uint64_t(h[3]) << 32);
+    return THR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+namespace thr {
+const KernelEntry* kernel_table(int* count) {
+    static const KernelEntry tab[] = {
+        {1, launch_threshold_1, occupancy_threshold_1},
+        {2, launch_threshold_2, occupancy_threshold_2},
+        {3, launch_threshold_3, occupancy_threshold_3},
+        {4, launch_threshold_4, occupancy_threshold_4},
+        {5, launch_threshold_5, occupancy_threshold_5},
+        {6, launch_threshold_6, occupancy_threshold_6},
+        {7, launch_threshold_7, occupancy_threshold_7},
+        {8, launch_threshold_8, occupancy_threshold_8},
+        {10, launch_threshold_10, occupancy_threshold_10},
+        {12, launch_threshold_12, occupancy_threshold_12},
+        {16, launch_threshold_16, occupancy_threshold_16},
+    };
+    *count = int(sizeof tab / sizeof tab[0]);
+    return tab;
+}
+}  // namespace thr
+
+extern "C" {
+
+const char* thr_last_error(void) { return g_err.c_str(); }
+
+double thr_last_kernel_ms(void) { return g_kernel_ms; }
+
+thr_status thr_rle_encode(const uint64_t* words, uint64_t nwords, uint64_t r,
+                          uint64_t* out, uint64_t cap, uint64_t* out_len) {
+    if (!out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null output");
+    const int rc = encode_words(words, nwords, r, out, cap, out_len);
+    if (rc == 1) return fail(THR_E_INVAL, "need ceil(r/64) words with bits >= r clear");
+    if (rc == 4) return fail(THR_E_NOSPACE, "encoded stream needs %llu words",
+                             (unsigned long long)*out_len);
+    return THR_OK;
+}
+
+thr_status thr_rle_validate(const uint64_t* stream, uint64_t len, uint64_t r) {
+    if (!stream && len) return fail(THR_E_INVAL, "null stream");
+    if ((r + 63) / 64 > kMaxWords) return fail(THR_E_INVAL, "r too large");
+    StreamScan sc;
+    std::string why;
+    if (scan_stream(stream, len, r, &sc, &why) != 0)
+        return fail(THR_E_FORMAT, "%s", why.c_str());
+    return THR_OK;
+}
+
+thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
+                         uint32_t nbitmaps, uint64_t r, void* cuda_stream,
+                         thr_index** out) {
+    if (!out || !offsets || nbitmaps == 0) return fail(THR_E_INVAL, "null argument or no bitmaps");
+    if (r == 0) return fail(THR_E_INVAL, "r must be at least 1");
+    const uint64_t W = (r + 63) / 64;
+    if (W > kMaxWords) return fail(THR_E_INVAL, "r too large (ceil(r/64) > 2^31 - 2)");
+    const uint64_t total = offsets[nbitmaps];
+    if (offsets[0] != 0) return fail(THR_E_INVAL, "offsets[0] must be 0");
+    for (uint32_t b = 0; b < nbitmaps; ++b)
+        if (offsets[b + 1] < offsets[b]) return fail(THR_E_INVAL, "offsets decrease at %u", b);
+    if (total && !words) return fail(THR_E_INVAL, "null words");
+    if (total >= (1ull << 40)) return fail(THR_E_INVAL, "index larger than 2^40 words");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    // validate every stream and record its marker positions (host threads)
+    std::vector<StreamScan> scans(nbitmaps);
+    std::vector<std::string> whys(nbitmaps);
+    std::vector<int> rcs(nbitmaps, 0);
+    {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const unsigned nt = std::min<unsigned>(hw, std::max<uint32_t>(1, nbitmaps));
+        std::atomic<uint32_t> next{0};
+        auto worker = [&]() {
+            for (;;) {
+                const uint32_t b = next.fetch_add(1);
+                if (b >= nbitmaps) return;
+                rcs[b] = scan_stream(words + offsets[b], offsets[b + 1] - offsets[b], r,
+                                     &scans[b], &whys[b]);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (unsigned i = 1; i < nt; ++i) pool.emplace_back(worker);
+        worker();
+        for (auto& th : pool) th.join();
+    }
+    for (uint32_t b = 0; b < nbitmaps; ++b)
+        if (rcs[b]) return fail(THR_E_FORMAT, "bitmap %u: %s", b, whys[b].c_str());
+
+    thr_index* idx = new (std::nothrow) thr_index;
+    if (!idx) return fail(THR_E_NOMEM, "host allocation");
+    CK(cudaGetDevice(&idx->device), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device),
+       "device attributes");
+    idx->nbitmaps = nbitmaps;
+    idx->r = r;
+    idx->W = uint32_t(W);
+    idx->NG = uint32_t((W + kGW - 1) / kGW);
+    idx->total_words = total;
+    idx->desc.resize(nbitmaps);
+    idx->set_rows.resize(nbitmaps);
+    uint64_t moff = 0;
+    for (uint32_t b = 0; b < nbitmaps; ++b) {
+        BitmapDesc& d = idx->desc[b];
+        d.woff = offsets[b];
+        d.moff = moff;
+        d.nmark = uint32_t(scans[b].marker_pos.size());
+        d.len = uint32_t(offsets[b + 1] - offsets[b]);
+        moff += d.nmark + 1;
+        idx->set_rows[b] = scans[b].set_rows;
+    }
+    idx->total_markers = moff - nbitmaps;
+    std::vector<uint32_t> mpos;
+    mpos.reserve(idx->total_markers);
+    for (uint32_t b = 0; b < nbitmaps; ++b)
+        mpos.insert(mpos.end(), scans[b].marker_pos.begin(), scans[b].marker_pos.end());
+    scans.clear();
+
+    auto cleanup = [&](thr_status s) {
+        idx_free(idx);
+        return s;
+    };
+    uint32_t* d_mpos = nullptr;
+    const uint64_t ttab_n = uint64_t(idx->NG + 1) * nbitmaps;
+    cudaError_t e;
+    if ((e = cudaMalloc(&idx->d_words, sizeof(uint64_t) * std::max<uint64_t>(total, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&idx->d_mtab, sizeof(uint2) * moff)) != cudaSuccess ||
+        (e = cudaMalloc(&idx->d_ttab, sizeof(uint32_t) * ttab_n)) != cudaSuccess ||
+        (e = cudaMalloc(&idx->d_desc, sizeof(BitmapDesc) * nbitmaps)) != cudaSuccess ||
+        (e = cudaMalloc(&d_mpos, sizeof(uint32_t) * std::max<uint64_t>(mpos.size(), 1))) != cudaSuccess) {
+        if (d_mpos) cudaFree(d_mpos);
+        return cleanup(cuda_fail(e, "index allocation"));
+    }
+    if ((e = cudaMemcpyAsync(idx->d_words, words, sizeof(uint64_t) * total,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_mpos, mpos.data(), sizeof(uint32_t) * mpos.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(idx->d_desc, idx->desc.data(), sizeof(BitmapDesc) * nbitmaps,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        cudaFree(d_mpos);
+        return cleanup(cuda_fail(e, "index upload"));
+    }
+    e = launch_index_build(idx->d_words, d_mpos, idx->d_desc, idx->d_mtab, idx->d_ttab,
+                           nbitmaps, idx->W, idx->NG, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_mpos);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "index build kernels"));
+    *out = idx;
+    return THR_OK;
+}
+
+void idx_free(thr_index* idx) {
+    if (!idx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(idx->device);
+    cudaDeviceSynchronize();
+    cudaFree(idx->d_words);
+    cudaFree(idx->d_mtab);
+    cudaFree(idx->d_ttab);
+    cudaFree(idx->d_desc);
+    cudaSetDevice(cur);
+    delete idx;
+}
+
+thr_status idx_info(const thr_index* idx, uint32_t* nbitmaps, uint64_t* r,
+                    uint64_t* total_words) {
+    if (!idx) return fail(THR_E_INVAL, "null index");
+    if (nbitmaps) *nbitmaps = idx->nbitmaps;
+    if (r) *r = idx->r;
+    if (total_words) *total_words = idx->total_words;
+    return THR_OK;
+}
+
+thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
+                     uint32_t T, uint64_t* out, uint64_t cap, uint64_t* out_len,
+                     uint32_t flags, void* cuda_stream) {
+    if (!idx || !ids || !out_len || (cap > 0 && !out))
+        return fail(THR_E_INVAL, "null argument");
+    if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
+    if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE))
+        return fail(THR_E_INVAL, "unknown flags");
+    const bool profile = flags & THR_PROFILE;
+    for (uint32_t i = 0; i < n; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool dev_out = flags & THR_OUT_DEVICE;
+    if (dev_out && cap > 0 && !is_device_ptr(out))
+        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+    if (dev_out) {
+        thr_status s = run_query(idx, ids, n, T, out, cap, out_len, st, profile);
+        if (s == THR_OK && *out_len > cap)
+            return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)*out_len);
+        return s;
+    }
+    // host output: compute into device scratch, then copy back
+    const uint64_t need = uint64_t(idx->W) + 1;
+    const uint64_t dcap = std::min<uint64_t>(cap, need);
+    uint64_t* dbuf = nullptr;
+    {
+        Scratch scr(st);
+        CK(scr.alloc((void**)&dbuf, sizeof(uint64_t) * std::max<uint64_t>(dcap, 1)),
+           "scratch (output)");
+        uint64_t len = 0;
+        thr_status s = run_query(idx, ids, n, T, dbuf, dcap, &len, st, profile);
+        if (s != THR_OK) return s;
+        *out_len = len;
+        if (len > cap)
+            return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)len);
+        CK(cudaMemcpyAsync(out, dbuf, sizeof(uint64_t) * len, cudaMemcpyDeviceToHost, st),
+           "copy result");
+        CK(cudaStreamSynchronize(st), "copy result");
+    }
+    return THR_OK;
+}
+
+thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                           const uint32_t* ids, const uint32_t* T, uint64_t* pool,
+                           uint64_t pool_cap, uint64_t* out_off, uint64_t* out_len,
+                           uint32_t flags, void* cuda_stream) {
+    if (!idx || !id_off || !T || !out_off || !out_len || (pool_cap > 0 && !pool))
+        return fail(THR_E_INVAL, "null argument");
+    if (nq == 0) return THR_OK;
+    if (!ids && id_off[nq] > 0) return fail(THR_E_INVAL, "null ids");
+    for (uint32_t q = 0; q < nq; ++q)
+        if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
+    uint64_t at = 0;
+    bool nospace = false;
+    for (uint32_t q = 0; q < nq; ++q) {
+        const uint64_t room = at < pool_cap ? pool_cap - at : 0;
+        uint64_t len = 0;
+        thr_status s = thr_query(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
+                                 room ? pool + at : nullptr, room, &len,
+                                 flags & (THR_OUT_DEVICE | THR_PROFILE), cuda_stream);
+        out_off[q] = at;
+        out_len[q] = len;
+        if (s == THR_E_NOSPACE) {
+            nospace = true;
+        } else if (s != THR_OK) {
+            return s;
+        }
+        at += len;
+    }
+    if (nospace) return fail(THR_E_NOSPACE, "pool needs %llu words", (unsigned long long)at);
+    return THR_OK;
+}
+
+}  // extern "C"

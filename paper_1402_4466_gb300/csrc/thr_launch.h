@@ -1,0 +1,40 @@
+// Launch entry points of the instantiated query kernels (one per counter
+// width S), defined in thr_inst_*.cu so that they compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "thr_device.cuh"
+
+namespace thr {
+
+using LaunchFn = cudaError_t (*)(const QueryParams&, int grid, cudaStream_t);
+using OccupancyFn = cudaError_t (*)(int* blocks_per_sm);
+
+struct KernelEntry {
+    int S;
+    LaunchFn launch;
+    OccupancyFn occupancy;
+};
+
+// Instantiated counter widths, ascending; a query uses the first S with
+// 2^S > the largest threshold its counters test.
+const KernelEntry* kernel_table(int* count);
+
+#define THR_DECLARE_WIDTH(S)                                            \
+    cudaError_t launch_threshold_##S(const QueryParams&, int, cudaStream_t); \
+    cudaError_t occupancy_threshold_##S(int*);
+
+THR_DECLARE_WIDTH(1)
+THR_DECLARE_WIDTH(2)
+THR_DECLARE_WIDTH(3)
+THR_DECLARE_WIDTH(4)
+THR_DECLARE_WIDTH(5)
+THR_DECLARE_WIDTH(6)
+THR_DECLARE_WIDTH(7)
+THR_DECLARE_WIDTH(8)
+THR_DECLARE_WIDTH(10)
+THR_DECLARE_WIDTH(12)
+THR_DECLARE_WIDTH(16)
+
+}  // namespace thr

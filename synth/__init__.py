@@ -125,17 +125,27 @@ def log_uniform_densities(seed: int, n: int, lo: float = 1e-4, hi: float = 0.3) 
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
 
 
-def many_criteria(seed: int, n: int, r: int, lo: float = 1e-4, hi: float = 0.3):
+def _many_one(args):
+    seed, k, r, p, clustered_kind = args
+    return clustered(seed, k, r, p) if clustered_kind else bernoulli(seed, k, r, p)
+
+
+def many_criteria(seed: int, n: int, r: int, lo: float = 1e-4, hi: float = 0.3,
+                  workers: int = 0):
     """N bitmaps, densities log-uniform in [lo, hi]; first half Bernoulli,
-    second half clustered (mean run 256 rows).  Returns (words list, densities)."""
+    second half clustered (mean run 256 rows).  Returns (words list, densities).
+    workers > 1 draws the bitmaps in a spawned process pool (same result)."""
     dens = log_uniform_densities(seed, n, lo, hi)
     half = n // 2
-    out = []
-    for k in range(n):
-        if k < half:
-            out.append(bernoulli(seed, k, r, float(dens[k])))
-        else:
-            out.append(clustered(seed, k, r, float(dens[k])))
+    jobs = [(seed, k, r, float(dens[k]), k >= half) for k in range(n)]
+    if workers and workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers,
+                                 mp_context=mp.get_context("spawn")) as ex:
+            out = list(ex.map(_many_one, jobs))
+    else:
+        out = [_many_one(j) for j in jobs]
     return out, dens
 
 

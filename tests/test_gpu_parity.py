@@ -1,0 +1,198 @@
+"""GPU parity: every result of the CUDA library, called through its C ABI,
+equals the CPU oracle's word for word (exact integer/bitwise arithmetic, so
+the tolerance is zero).  Inputs are seeded synthetic bitmaps; each side
+encodes them with its own codec and the two encodings must agree.
+
+Sizes: tiny random cases (all T), several-tile cases with ragged tails, the
+8 x 2^20 plain workload, the 64 x 2^26 many-criteria workload at full size in
+the launch configuration the benchmark times, and edge cases (r = 1, ragged
+last words, empty and full bitmaps, duplicated ids, T = 0, T > N, more
+inputs than one chunk, undersized outputs)."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins
+import paper_1402_4466_gb300 as thr
+import synth
+from golden import bits_row0_first, hex_words, read_kv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+    return torch
+
+
+class Pair:
+    """The same bitmaps as a GPU index and an oracle index."""
+
+    def __init__(self, word_arrays, r):
+        self.r = r
+        gw, goff = thr.encode_many(word_arrays, r)
+        ostreams = [oracle.encode(w, r) for w in word_arrays]
+        ow, ooff = oracle.concat(ostreams)
+        assert np.array_equal(gw, ow) and np.array_equal(goff, ooff), \
+            "library and oracle encoders disagree"
+        self.g = thr.idx_build_rle(gw, goff, r)
+        self.o = oracle.Index(ostreams, r)
+
+    def check(self, ids, T):
+        got = thr.thr_query(self.g, ids, T)
+        want = self.o.threshold(ids, T)
+        if not np.array_equal(got, want):
+            gr = oracle.decode(got, self.r) if oracle.validate(got, self.r) == 0 else None
+            wr = oracle.decode(want, self.r)
+            msg = f"T={T} n={len(ids)} r={self.r}: lengths {len(got)} vs {len(want)}"
+            if gr is None:
+                msg += "; GPU stream is not canonical"
+            else:
+                d = np.setxor1d(gr, wr)
+                msg += f"; {len(d)} rows differ, first {d[:8].tolist()}"
+            pytest.fail(msg)
+        return got
+
+
+def from_ints(bitsets, r):
+    return Pair([oracle_pins.int_to_words(b, r) for b in bitsets], r)
+
+
+def test_paper_examples():
+    g = read_kv("fig1_threshold.txt")
+    p = from_ints([bits_row0_first(g[k]) for k in ("B1", "B2", "B3")], int(g["r"]))
+    for T in range(0, 5):
+        p.check([0, 1, 2], T)
+    g = read_kv("rbmrg_ewah.txt")
+    B = [oracle_pins.words_to_int(hex_words(g[k])) for k in ("B1", "B2", "B3", "B4")]
+    p = from_ints(B, int(g["r"]))
+    got = p.check([0, 1, 2, 3], 3)
+    assert oracle.decode(got, p.r).tolist() == oracle_pins.rows_of(
+        oracle_pins.words_to_int(hex_words(g["result"])))
+    for T in range(0, 6):
+        p.check([0, 1, 2, 3], T)
+
+
+def test_random_tiny_all_thresholds():
+    rng = np.random.default_rng(101)
+    for _ in range(30):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 5, 63, 64, 65, 200, 1000, 4096, 8191, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        for T in range(0, n + 2):
+            p.check(list(range(n)), T)
+        ids = rng.integers(0, n, size=int(rng.integers(1, 20))).tolist()
+        for T in (0, 1, 2, len(ids) // 2, len(ids), len(ids) + 1):
+            p.check(ids, T)
+
+
+@pytest.mark.parametrize("r", [(1 << 18) + 37, 9 * 512 * 64, 3 * 512 * 64 + 64 * 5 + 1])
+def test_several_tiles_ragged(r):
+    words, _ = synth.many_criteria(11, 24, r)
+    p = Pair(words, r)
+    for T in list(range(0, 8)) + [11, 12, 13, 20, 23, 24, 25]:
+        p.check(list(range(24)), T)
+
+
+def test_plain_workload():
+    r = synth.PLAIN_R
+    p = Pair(synth.plain(0, synth.PLAIN_N, r, synth.PLAIN_P), r)
+    for T in range(0, synth.PLAIN_N + 2):
+        p.check(list(range(synth.PLAIN_N)), T)
+
+
+def test_many_criteria_full_size():
+    """64 bitmaps over 2^26 rows; the thresholds the benchmark times."""
+    r = synth.MANY_R
+    words, _ = synth.many_criteria(0, synth.MANY_N, r)
+    p = Pair(words, r)
+    ids = list(range(synth.MANY_N))
+    for T in synth.MANY_TS:
+        p.check(ids, T)
+    p.check(ids, 1)
+    p.check(ids, 64)
+
+
+def test_more_inputs_than_one_chunk():
+    r = 50_000
+    words, _ = synth.many_criteria(5, 40, r)
+    p = Pair(words, r)
+    rng = np.random.default_rng(5)
+    ids = rng.integers(0, 40, size=600).tolist()
+    for T in (0, 1, 2, 30, 150, 300, 450, 599, 600, 601):
+        p.check(ids, T)
+
+
+def test_edge_bitmaps():
+    for r in (1, 2, 63, 64, 65, 128 * 64, 128 * 64 + 1, 512 * 64, 512 * 64 + 63):
+        full = (1 << r) - 1
+        alt = int("01" * ((r + 1) // 2), 2) & full
+        B = [0, full, 1 << (r - 1), full ^ 1, alt]
+        p = from_ints(B, r)
+        for T in range(0, 7):
+            p.check([0, 1, 2, 3, 4], T)
+        p.check([1], 1)
+        p.check([0], 1)
+        p.check([1, 1, 1], 3)
+
+
+def test_duplicate_ids_and_single_input():
+    r = 70_000
+    words, _ = synth.many_criteria(9, 6, r)
+    p = Pair(words, r)
+    for T in range(0, 5):
+        p.check([2, 2, 2], T)
+        p.check([4], T)
+        p.check([0, 1, 1, 3, 3, 3], T)
+
+
+def test_device_output_and_nospace(cuda):
+    torch = cuda
+    r = (1 << 16) + 11
+    words, _ = synth.many_criteria(3, 10, r)
+    p = Pair(words, r)
+    ids = list(range(10))
+    want = p.o.threshold(ids, 3)
+    out = torch.zeros(len(want) + 5, dtype=torch.int64, device="cuda")
+    n = thr.thr_query(p.g, ids, 3, out=out)
+    assert n == len(want)
+    assert np.array_equal(out[:n].cpu().numpy().view(np.uint64), want)
+    small = torch.zeros(len(want) - 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(thr.ThrError) as e:
+        thr.thr_query(p.g, ids, 3, out=small)
+    assert e.value.status == thr.THR_E_NOSPACE
+    st, need = thr.thr_query_raw(p.g, ids, 3, small.data_ptr(), small.numel(),
+                                 thr.THR_OUT_DEVICE)
+    assert st == thr.THR_E_NOSPACE and need == len(want)
+    host = np.zeros(len(want) - 1, dtype=np.uint64)
+    st, need = thr.thr_query_raw(p.g, ids, 3, host.ctypes.data, host.size, 0)
+    assert st == thr.THR_E_NOSPACE and need == len(want)
+
+
+def test_batch_matches_single_queries(cuda):
+    r = 100_000
+    words, _ = synth.many_criteria(4, 16, r)
+    p = Pair(words, r)
+    rng = np.random.default_rng(4)
+    queries = []
+    for _ in range(12):
+        n = int(rng.integers(1, 30))
+        ids = rng.integers(0, 16, size=n).tolist()
+        queries.append((ids, int(rng.integers(0, n + 2))))
+    off, ln, pool = thr.thr_query_batch(p.g, queries)
+    for q, (ids, T) in enumerate(queries):
+        got = pool[int(off[q]): int(off[q]) + int(ln[q])]
+        assert np.array_equal(got, p.o.threshold(ids, T))
+
+
+def test_invalid_arguments():
+    p = from_ints([5, 7], 64)
+    with pytest.raises(thr.ThrError) as e:
+        thr.thr_query(p.g, [0, 2], 1)
+    assert e.value.status == thr.THR_E_INVAL
+    with pytest.raises(thr.ThrError) as e:
+        thr.thr_query(p.g, [], 1)
+    assert e.value.status == thr.THR_E_INVAL
