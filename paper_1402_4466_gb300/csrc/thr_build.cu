@@ -85,16 +85,181 @@ __global__ void k_tile_table(const uint2* __restrict__ mtab,
     ttab[i] = lo;
 }
 
-cudaError_t launch_index_build(const uint64_t* words, const uint32_t* mpos,
-                               const BitmapDesc* desc, uint2* mtab,
-                               uint32_t* ttab, uint32_t nbitmaps, uint32_t W,
-                               uint32_t NG, cudaStream_t st) {
+// Subtile classes.  One CTA per bitmap walks its subtiles in order; for
+// every subtile it counts the literal and ones-fill words of the markers that
+// overlap it (the RBMrg/EWAH run cases of Sec. 6.4 decided once, at build):
+// class 0 all zero fill, 1 all ones fill, 2 one literal run (the subtile's
+// words are contiguous literals), 3 mixed.  Mixed subtiles are numbered in
+// order (block scan); the descriptor holds class | flags | counts | field
+// (field: class 2 = stream index of the first literal, class 3 = the rank,
+// replaced by the mask record index in k_subtile_masks).
+__global__ void k_subtile_class(const uint2* __restrict__ mtab,
+                                const uint32_t* __restrict__ ttab,
+                                const BitmapDesc* __restrict__ desc,
+                                uint64_t* __restrict__ sdesc,
+                                uint32_t* __restrict__ mixed_count, uint32_t W,
+                                uint32_t NG) {
+    const uint32_t b = blockIdx.x;
+    const BitmapDesc d = desc[b];
+    const uint32_t* tt = ttab + uint64_t(b) * (NG + 1);
+    __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t base = 0; base < NG; base += blockDim.x) {
+        const uint32_t g = base + threadIdx.x;
+        uint32_t mixed = 0;
+        uint64_t word = 0;
+        if (g < NG) {
+            const uint32_t x0 = g * uint32_t(kGW);
+            const uint32_t x1 = min(x0 + uint32_t(kGW), W);
+            const uint32_t m0 = tt[g], m1 = tt[g + 1];
+            uint32_t mend = d.nmark;
+            if (m1 < d.nmark) mend = m1 + (((mtab[d.moff + m1].y & 0x7fffffffu) < x1) ? 1u : 0u);
+            uint32_t nl = 0, none = 0;
+            for (uint32_t m = m0; m < mend; ++m) {
+                const uint2 e0 = mtab[d.moff + m], e1 = mtab[d.moff + m + 1];
+                const uint32_t u = e0.y & 0x7fffffffu, ue = e1.y & 0x7fffffffu;
+                const uint32_t fe = ue - (e1.x - e0.x - 1);
+                const uint32_t la = max(fe, x0), lb = min(ue, x1);
+                if (lb > la) nl += lb - la;
+                if (e0.y >> 31) {
+                    const uint32_t oa = max(u, x0), ob = min(fe, x1);
+                    if (ob > oa) none += ob - oa;
+                }
+            }
+            const uint32_t nm = mend - m0, len = x1 - x0;
+            const uint2 f0 = mtab[d.moff + m0], f1 = mtab[d.moff + m0 + 1];
+            const uint32_t fe0 = (f1.y & 0x7fffffffu) - (f1.x - f0.x - 1);
+            uint64_t cls, field = 0;
+            if (nl == 0 && none == 0) {
+                cls = 0;
+            } else if (none == len) {
+                cls = 1;
+            } else if (nl == len && nm == 1) {
+                cls = 2;
+                field = uint64_t(f0.x) + 1 + (x0 - fe0);
+            } else {
+                cls = 3;
+                mixed = 1;
+            }
+            word = cls | (uint64_t(none ? 1 : 0) << 2) | (uint64_t(nl) << 3) |
+                   (uint64_t(none) << 11) | (field << 19);
+        }
+        uint32_t incl = mixed;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= uint32_t(o)) incl += v;
+        }
+        if (lane == 31) warp_sum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t ws = lane < nwarps ? warp_sum[lane] : 0;
+            uint32_t wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= uint32_t(o)) wi += v;
+            }
+            if (lane < nwarps) warp_sum[lane] = wi - ws;
+        }
+        __syncthreads();
+        const uint32_t rank = carry + warp_sum[wid] + incl - mixed;
+        if (g < NG) sdesc[uint64_t(b) * NG + g] = mixed ? (word | (uint64_t(rank) << 19)) : word;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = rank + mixed;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mixed_count[b] = carry;
+}
+
+// Mask records of the mixed subtiles (layout: MaskRec in thr_device.cuh):
+// literal-word mask, group-start mask (markers starting strictly after the
+// subtile's first word), ones-fill mask, the stream index of the first
+// literal at or after the subtile start (base) and the per-32-word prefix
+// counts.  The literal at subtile word x then sits at stream index
+// base + (literal words in [x0, x)) + (group starts in (x0, x]), because every
+// group after the first adds one marker word before its literals.
+__global__ void k_subtile_masks(const uint2* __restrict__ mtab,
+                                const uint32_t* __restrict__ ttab,
+                                const BitmapDesc* __restrict__ desc,
+                                const uint64_t* __restrict__ mixed_base,
+                                uint64_t* __restrict__ sdesc,
+                                MaskRec* __restrict__ masks, uint32_t nbitmaps,
+                                uint32_t W, uint32_t NG) {
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= uint64_t(NG) * nbitmaps) return;
+    const uint64_t sd = sdesc[i];
+    if ((sd & 3u) != 3u) return;
+    const uint32_t b = uint32_t(i / NG), g = uint32_t(i % NG);
+    const BitmapDesc d = desc[b];
+    const uint32_t* tt = ttab + uint64_t(b) * (NG + 1);
+    const uint32_t x0 = g * uint32_t(kGW);
+    const uint32_t x1 = min(x0 + uint32_t(kGW), W);
+    const uint32_t m0 = tt[g], m1 = tt[g + 1];
+    uint32_t mend = d.nmark;
+    if (m1 < d.nmark) mend = m1 + (((mtab[d.moff + m1].y & 0x7fffffffu) < x1) ? 1u : 0u);
+    uint32_t lm[4] = {0, 0, 0, 0}, gm[4] = {0, 0, 0, 0}, om[4] = {0, 0, 0, 0};
+    uint32_t base = 0;
+    for (uint32_t m = m0; m < mend; ++m) {
+        const uint2 e0 = mtab[d.moff + m], e1 = mtab[d.moff + m + 1];
+        const uint32_t u = e0.y & 0x7fffffffu, ue = e1.y & 0x7fffffffu;
+        const uint32_t fe = ue - (e1.x - e0.x - 1);
+        if (m == m0) base = e0.x + 1 + (x0 > fe ? x0 - fe : 0u);
+        if (m > m0) {  // u is inside (x0, x1)
+            const uint32_t r = u - x0;
+            gm[r >> 5] |= 1u << (r & 31);
+        }
+        for (uint32_t x = max(fe, x0); x < min(ue, x1); ++x) {
+            const uint32_t r = x - x0;
+            lm[r >> 5] |= 1u << (r & 31);
+        }
+        if (e0.y >> 31)
+            for (uint32_t x = max(u, x0); x < min(fe, x1); ++x) {
+                const uint32_t r = x - x0;
+                om[r >> 5] |= 1u << (r & 31);
+            }
+    }
+    MaskRec rec;
+    uint32_t run = 0;
+    for (int w = 0; w < 4; ++w) {
+        rec.lm[w] = lm[w];
+        rec.gm[w] = gm[w];
+        rec.om[w] = om[w];
+        rec.pre[w] = uint16_t(run);
+        run += __popc(lm[w]) + __popc(gm[w]);
+    }
+    rec.base = base;
+    rec.pad = 0;
+    const uint64_t idx = mixed_base[b] + (sd >> 19);
+    masks[idx] = rec;
+    sdesc[i] = (sd & ((1ull << 19) - 1)) | (idx << 19);
+}
+
+cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
+                                 const BitmapDesc* desc, uint2* mtab, uint32_t* ttab,
+                                 uint64_t* sdesc, uint32_t* mixed_count,
+                                 uint32_t nbitmaps, uint32_t W, uint32_t NG,
+                                 cudaStream_t st) {
     k_marker_scan<<<nbitmaps, 256, 0, st>>>(words, mpos, desc, mtab, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t n = (uint64_t(NG) + 1) * nbitmaps;
-    const uint64_t blocks = (n + 255) / 256;
-    k_tile_table<<<unsigned(blocks), 256, 0, st>>>(mtab, desc, ttab, nbitmaps, NG);
+    k_tile_table<<<unsigned((n + 255) / 256), 256, 0, st>>>(mtab, desc, ttab, nbitmaps, NG);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_subtile_class<<<nbitmaps, 256, 0, st>>>(mtab, ttab, desc, sdesc, mixed_count, W, NG);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_index_build_b(const uint2* mtab, const uint32_t* ttab,
+                                 const BitmapDesc* desc, const uint64_t* mixed_base,
+                                 uint64_t* sdesc, MaskRec* masks, uint32_t nbitmaps,
+                                 uint32_t W, uint32_t NG, cudaStream_t st) {
+    const uint64_t ns = uint64_t(NG) * nbitmaps;
+    k_subtile_masks<<<unsigned((ns + 255) / 256), 256, 0, st>>>(mtab, ttab, desc, mixed_base,
+                                                               sdesc, masks, nbitmaps, W, NG);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -35,7 +36,9 @@ struct thr_index {
     uint64_t total_markers = 0;
     uint64_t* d_words = nullptr;
     uint2* d_mtab = nullptr;
-    uint32_t* d_ttab = nullptr;
+    uint64_t* d_sdesc = nullptr;  // NG subtile descriptors per bitmap
+    MaskRec* d_masks = nullptr;   // mask records of the mixed subtiles
+    uint64_t mixed_subtiles = 0;
     BitmapDesc* d_desc = nullptr;
     std::vector<BitmapDesc> desc;
     std::vector<uint64_t> set_rows;
@@ -46,6 +49,23 @@ namespace {
 
 thread_local std::string g_err;
 thread_local double g_kernel_ms = -1.0;
+
+// THR_TRACE=1 in the environment: one stderr line per step of a query.
+bool trace_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("THR_TRACE");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+#define TRACE(...)                                      \
+    do {                                                \
+        if (trace_on()) {                               \
+            std::fprintf(stderr, "[thr] " __VA_ARGS__); \
+            std::fputc('\n', stderr);                  \
+            std::fflush(stderr);                        \
+        }                                               \
+    } while (0)
 
 thr_status fail(thr_status st, const char* fmt, ...) {
     char buf[512];
@@ -69,23 +89,31 @@ thr_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-// Pinned per-thread buffer for the few words read back after a query.
-struct PinnedCtl {
+// Pinned per-thread staging: the query's ids on the way in, the control
+// words (result length) on the way out.  Grows on demand.
+struct Pinned {
     uint32_t* p = nullptr;
-    ~PinnedCtl() {
+    size_t bytes = 0;
+    ~Pinned() {
         if (p) cudaFreeHost(p);
     }
 };
-thread_local PinnedCtl g_ctl;
+thread_local Pinned g_pin;
 
-cudaError_t pinned_ctl(uint32_t** out) {
-    if (!g_ctl.p) {
-        cudaError_t e = cudaMallocHost(&g_ctl.p, 64);
+cudaError_t pinned(size_t bytes, uint32_t** out) {
+    if (g_pin.bytes < bytes) {
+        if (g_pin.p) cudaFreeHost(g_pin.p);
+        g_pin.p = nullptr;
+        g_pin.bytes = 0;
+        cudaError_t e = cudaMallocHost(&g_pin.p, bytes);
         if (e != cudaSuccess) return e;
+        g_pin.bytes = bytes;
     }
-    *out = g_ctl.p;
+    *out = g_pin.p;
     return cudaSuccess;
 }
+
+size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
 
 int bit_length(uint64_t v) {
     int n = 0;
@@ -138,43 +166,55 @@ WidthChoice choose_width(uint32_t n, uint32_t T) {
 thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
                      uint32_t T, uint64_t* dout, uint64_t cap, uint64_t* len,
                      cudaStream_t st, bool profile) {
-    const uint32_t ntiles = (idx->W + kTW - 1) / kTW;
+    const uint32_t NG = idx->NG;
+    // one scratch block: control words | ids | aggregates | prefixes | U
+    const size_t o_ids = 256;
+    const size_t o_aggs = o_ids + round256(sizeof(uint32_t) * n);
+    const size_t o_pref = o_aggs + round256(sizeof(uint32_t) * kAggWords * uint64_t(NG));
+    const uint64_t NB = (NG + 255) / 256;  // scan blocks of pass B
+    const size_t o_bagg = o_pref + round256(sizeof(uint32_t) * kAggWords * uint64_t(NG));
+    const size_t o_bpref = o_bagg + round256(sizeof(uint32_t) * kAggWords * NB);
+    const size_t o_U = o_bpref + round256(sizeof(uint32_t) * kAggWords * NB);
+    const size_t total = o_U + sizeof(uint64_t) * uint64_t(NG) * kGW;
     Scratch scr(st);
-    uint32_t* d_ids = nullptr;
-    uint32_t* d_states = nullptr;
-    uint32_t* d_ctl = nullptr;
-    CK(scr.alloc((void**)&d_ids, sizeof(uint32_t) * n), "scratch (ids)");
-    CK(scr.alloc((void**)&d_states, sizeof(uint32_t) * kStateWords * ntiles),
-       "scratch (tile states)");
-    CK(scr.alloc((void**)&d_ctl, 64), "scratch (control)");
-    CK(cudaMemcpyAsync(d_ids, ids, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st),
+    unsigned char* blk = nullptr;
+    CK(scr.alloc((void**)&blk, total), "query scratch");
+    uint32_t* d_ctl = reinterpret_cast<uint32_t*>(blk);
+    uint32_t* d_ids = reinterpret_cast<uint32_t*>(blk + o_ids);
+    uint32_t* d_aggs = reinterpret_cast<uint32_t*>(blk + o_aggs);
+    uint32_t* d_pref = reinterpret_cast<uint32_t*>(blk + o_pref);
+    uint64_t* d_U = reinterpret_cast<uint64_t*>(blk + o_U);
+    uint32_t* h = nullptr;
+    CK(pinned(64 + sizeof(uint32_t) * size_t(n), &h), "pinned staging");
+    std::memcpy(h + 16, ids, sizeof(uint32_t) * n);
+    CK(cudaMemcpyAsync(d_ids, h + 16, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st),
        "upload ids");
-    CK(cudaMemsetAsync(d_states, 0, sizeof(uint32_t) * kStateWords * ntiles, st),
-       "clear tile states");
     CK(cudaMemsetAsync(d_ctl, 0, 64, st), "clear control words");
 
     const WidthChoice wc = choose_width(n, T);
     QueryParams p{};
     p.words = idx->d_words;
     p.mtab = idx->d_mtab;
-    p.ttab = idx->d_ttab;
+    p.sdesc = idx->d_sdesc;
+    p.masks = idx->d_masks;
     p.desc = idx->d_desc;
     p.ids = d_ids;
     p.n = n;
     p.T = T;
     p.zmode = wc.zmode;
     p.W = idx->W;
-    p.NG = idx->NG;
-    p.ntiles = ntiles;
+    p.NG = NG;
+    p.ntiles = NG;
     p.ragged = uint32_t(idx->r % 64);
-    p.spin_limit = 1u << 20;
-    p.out = dout;
-    p.cap = cap;
-    p.states = d_states;
     p.ctl = d_ctl;
+    p.U = d_U;
+    p.aggs = d_aggs;
     int per_sm = 0;
+    TRACE("query n=%u T=%u NG=%u S=%d zmode=%u", n, T, NG, wc.k->S, wc.zmode);
     CK(wc.k->occupancy(&per_sm), "occupancy query");
-    const int grid = int(std::min<uint64_t>(ntiles, uint64_t(std::max(per_sm, 1)) * idx->num_sms));
+    const int grid = int(std::min<uint64_t>((NG + kNW - 1) / kNW,
+                                            uint64_t(std::max(per_sm, 1)) * idx->num_sms));
+    TRACE("pass A grid=%d per_sm=%d", grid, per_sm);
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (profile) {
         CK(cudaEventCreate(&ev[0]), "event");
@@ -183,9 +223,23 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     }
     CK(wc.k->launch(p, std::max(grid, 1), st), "launch threshold kernel");
     if (profile) CK(cudaEventRecord(ev[1], st), "event record");
+    if (trace_on()) CK(cudaStreamSynchronize(st), "pass A");
+    TRACE("pass A done");
+    WriteParams w{};
+    w.U = d_U;
+    w.aggs = d_aggs;
+    w.pref = d_pref;
+    w.bagg = reinterpret_cast<uint32_t*>(blk + o_bagg);
+    w.bpref = reinterpret_cast<uint32_t*>(blk + o_bpref);
+    w.out = dout;
+    w.cap = cap;
+    w.W = idx->W;
+    w.NG = NG;
+    w.ctl = d_ctl;
+    CK(launch_reencode(w, st), "launch re-encoding kernels");
+    if (trace_on()) CK(cudaStreamSynchronize(st), "passes B, C");
+    TRACE("passes B, C done");
 
-    uint32_t* h = nullptr;
-    CK(pinned_ctl(&h), "pinned buffer");
     CK(cudaMemcpyAsync(h, d_ctl, 16, cudaMemcpyDeviceToHost, st), "read result length");
     CK(cudaStreamSynchronize(st), "query");
     if (profile) {
@@ -195,8 +249,6 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
     }
-    if (h[1] & kErrSpin)
-        return fail(THR_E_TIMEOUT, "tile look-back exceeded its spin limit");
     *len = uint64_t(h[2]) | (uint64_t(h[3]) << 32);
     return THR_OK;
 }
@@ -300,6 +352,13 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
     thr_index* idx = new (std::nothrow) thr_index;
     if (!idx) return fail(THR_E_NOMEM, "host allocation");
     CK(cudaGetDevice(&idx->device), "cudaGetDevice");
+    {  // keep query scratch in the device's stream-ordered pool between queries
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, idx->device) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     CK(cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device),
        "device attributes");
     idx->nbitmaps = nbitmaps;
@@ -331,14 +390,21 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         return s;
     };
     uint32_t* d_mpos = nullptr;
+    uint32_t* d_ttab = nullptr;  // build temporary
     const uint64_t ttab_n = uint64_t(idx->NG + 1) * nbitmaps;
+    const uint64_t sdesc_n = uint64_t(idx->NG) * nbitmaps;
     cudaError_t e;
+    auto free_tmp = [&]() {
+        if (d_mpos) cudaFree(d_mpos);
+        if (d_ttab) cudaFree(d_ttab);
+    };
     if ((e = cudaMalloc(&idx->d_words, sizeof(uint64_t) * std::max<uint64_t>(total, 1))) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_mtab, sizeof(uint2) * moff)) != cudaSuccess ||
-        (e = cudaMalloc(&idx->d_ttab, sizeof(uint32_t) * ttab_n)) != cudaSuccess ||
+        (e = cudaMalloc(&idx->d_sdesc, sizeof(uint64_t) * sdesc_n)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_desc, sizeof(BitmapDesc) * nbitmaps)) != cudaSuccess ||
+        (e = cudaMalloc(&d_ttab, sizeof(uint32_t) * ttab_n)) != cudaSuccess ||
         (e = cudaMalloc(&d_mpos, sizeof(uint32_t) * std::max<uint64_t>(mpos.size(), 1))) != cudaSuccess) {
-        if (d_mpos) cudaFree(d_mpos);
+        free_tmp();
         return cleanup(cuda_fail(e, "index allocation"));
     }
     if ((e = cudaMemcpyAsync(idx->d_words, words, sizeof(uint64_t) * total,
@@ -347,13 +413,46 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(idx->d_desc, idx->desc.data(), sizeof(BitmapDesc) * nbitmaps,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess) {
-        cudaFree(d_mpos);
+        free_tmp();
         return cleanup(cuda_fail(e, "index upload"));
     }
-    e = launch_index_build(idx->d_words, d_mpos, idx->d_desc, idx->d_mtab, idx->d_ttab,
-                           nbitmaps, idx->W, idx->NG, st);
+    uint32_t* d_mcount = nullptr;
+    uint64_t* d_mbase = nullptr;
+    auto free_all_tmp = [&]() {
+        free_tmp();
+        if (d_mcount) cudaFree(d_mcount);
+        if (d_mbase) cudaFree(d_mbase);
+    };
+    if ((e = cudaMalloc(&d_mcount, sizeof(uint32_t) * nbitmaps)) != cudaSuccess ||
+        (e = cudaMalloc(&d_mbase, sizeof(uint64_t) * nbitmaps)) != cudaSuccess) {
+        free_all_tmp();
+        return cleanup(cuda_fail(e, "index allocation"));
+    }
+    e = launch_index_build_a(idx->d_words, d_mpos, idx->d_desc, idx->d_mtab, d_ttab,
+                             idx->d_sdesc, d_mcount, nbitmaps, idx->W, idx->NG, st);
+    std::vector<uint32_t> mcount(nbitmaps);
+    std::vector<uint64_t> mbase(nbitmaps);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mcount.data(), d_mcount, sizeof(uint32_t) * nbitmaps,
+                            cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_mpos);
+    if (e == cudaSuccess) {
+        uint64_t acc = 0;
+        for (uint32_t b = 0; b < nbitmaps; ++b) {
+            mbase[b] = acc;
+            acc += mcount[b];
+        }
+        idx->mixed_subtiles = acc;
+        e = cudaMalloc(&idx->d_masks, sizeof(MaskRec) * std::max<uint64_t>(acc, 1));
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_mbase, mbase.data(), sizeof(uint64_t) * nbitmaps,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_index_build_b(idx->d_mtab, d_ttab, idx->d_desc, d_mbase, idx->d_sdesc,
+                                 idx->d_masks, nbitmaps, idx->W, idx->NG, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_all_tmp();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "index build kernels"));
     *out = idx;
     return THR_OK;
@@ -367,7 +466,8 @@ void idx_free(thr_index* idx) {
     cudaDeviceSynchronize();
     cudaFree(idx->d_words);
     cudaFree(idx->d_mtab);
-    cudaFree(idx->d_ttab);
+    cudaFree(idx->d_sdesc);
+    cudaFree(idx->d_masks);
     cudaFree(idx->d_desc);
     cudaSetDevice(cur);
     delete idx;

@@ -46,8 +46,23 @@ constexpr int kNW = 4;            // warps per CTA
 constexpr int kNT = 32 * kNW;     // threads per CTA
 constexpr int kTW = kGW * kNW;    // words per CTA tile
 constexpr int kWPL = 4;           // consecutive words per lane
-constexpr int kCH = 256;          // input records per warp and chunk
+constexpr int kCH = 128;          // input records per warp and chunk
 constexpr int kSMax = 16;         // largest counter width instantiated
+
+// Mask record of a mixed (bitmap, subtile): bit r of lm / gm / om is subtile
+// word x0 + r being a literal / starting a marker group / a ones-fill word;
+// base = stream index (relative to the bitmap's first word) of the first
+// literal at or after x0; pre[w] = literal words + group starts before word
+// 32 w of the subtile (excluding x0 itself).
+struct MaskRec {
+    uint32_t lm[4];
+    uint32_t gm[4];
+    uint32_t om[4];
+    uint32_t base;
+    uint16_t pre[4];
+    uint32_t pad;
+};
+static_assert(sizeof(MaskRec) == 64, "mask record is one 64-byte line");
 
 struct BitmapDesc {
     uint64_t woff;   // first word of the stream in `words`
@@ -64,14 +79,14 @@ struct RangeAgg {
     uint32_t start, nh, nl, lh, lp, cls;
 };
 
-// Per-tile look-back slot: flag (0 empty, 1 aggregate, 2 inclusive prefix),
-// then the aggregate and the inclusive prefix.
-constexpr int kStateWords = 16;
+// Aggregates and prefixes are stored as kAggWords uint32 per subtile.
+constexpr int kAggWords = 8;
 
 struct QueryParams {
     const uint64_t* words;
     const uint2* mtab;
-    const uint32_t* ttab;
+    const uint64_t* sdesc;  // subtile descriptors, NG per bitmap
+    const MaskRec* masks;   // mask records of the mixed subtiles
     const BitmapDesc* desc;
     const uint32_t* ids;  // device copy of the query's ids
     uint32_t n;
@@ -79,17 +94,29 @@ struct QueryParams {
     uint32_t zmode;   // 1: count zeros among the active inputs
     uint32_t W;       // uncompressed words
     uint32_t NG;      // subtiles
-    uint32_t ntiles;  // CTA tiles
+    uint32_t ntiles;  // subtiles (= NG)
     uint32_t ragged;  // r % 64
     uint32_t spin_limit;
-    uint64_t* out;    // device output buffer
-    uint64_t cap;
-    uint32_t* states;  // ntiles * kStateWords, zeroed
-    uint32_t* ctl;     // [0] tile counter, [1] error bits, [2..3] length
+    uint32_t* ctl;     // [0] subtile counter (zeroed before the launch)
+    uint64_t* U;       // scratch: W result words (only non-uniform subtiles stored)
+    uint32_t* aggs;    // scratch: per subtile re-encoding aggregate
 };
 
-// error bits in ctl[1]
-constexpr uint32_t kErrSpin = 1u;
+// Passes B and C of the re-encoding (thr_reencode.cu).
+struct WriteParams {
+    const uint64_t* U;
+    const uint32_t* aggs;
+    uint32_t* pref;    // per subtile: prefix within its scan block (pass B)
+    uint32_t* bagg;    // per scan block: total
+    uint32_t* bpref;   // per scan block: prefix before it
+    uint64_t* out;     // device output buffer
+    uint64_t cap;
+    uint32_t W;
+    uint32_t NG;
+    uint32_t* ctl;     // [2..3] encoded length (pass B), [4] pass B ticket
+};
+cudaError_t launch_reencode(const WriteParams& w, cudaStream_t st);
+
 
 // ------------------------------------------------------------ primitives
 
@@ -108,12 +135,6 @@ constexpr uint32_t kAndNot = 0x30; // a & ~b  (c unused)
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
-    return *reinterpret_cast<const volatile uint32_t*>(p);
-}
-__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
-    *reinterpret_cast<volatile uint32_t*>(p) = v;
-}
 
 // ---------------------------------------------------- bit-sliced counters
 //
@@ -224,33 +245,37 @@ __device__ __forceinline__ RangeAgg agg_combine(const RangeAgg& X, const RangeAg
     return Z;
 }
 
-__device__ __forceinline__ void agg_store(uint32_t* p, const RangeAgg& a) {
-    st_volatile(p + 0, a.start);
-    st_volatile(p + 1, a.nh);
-    st_volatile(p + 2, a.nl);
-    st_volatile(p + 3, a.lh);
-    st_volatile(p + 4, a.lp);
-    st_volatile(p + 5, a.cls);
+__device__ __forceinline__ void agg_store_plain(uint32_t* p, const RangeAgg& a) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(a.start, a.nh, a.nl, a.lh);
+    *reinterpret_cast<uint2*>(p + 4) = make_uint2(a.lp, a.cls);
 }
-__device__ __forceinline__ RangeAgg agg_load(const uint32_t* p) {
+__device__ __forceinline__ RangeAgg agg_load_plain(const uint32_t* p) {
+    const uint4 x = *reinterpret_cast<const uint4*>(p);
+    const uint2 y = *reinterpret_cast<const uint2*>(p + 4);
     RangeAgg a;
-    a.start = ld_volatile(p + 0);
-    a.nh = ld_volatile(p + 1);
-    a.nl = ld_volatile(p + 2);
-    a.lh = ld_volatile(p + 3);
-    a.lp = ld_volatile(p + 4);
-    a.cls = ld_volatile(p + 5);
+    a.start = x.x;
+    a.nh = x.y;
+    a.nl = x.z;
+    a.lh = x.w;
+    a.lp = y.x;
+    a.cls = y.y;
     return a;
 }
 
 // ------------------------------------------------------------- build (K1)
 
-// Build kernels (thr_build.cu): segmented scan of the marker extents into
-// mtab, then the subtile table.  Both run on `st`; errors come back from the
-// launch.
-cudaError_t launch_index_build(const uint64_t* words, const uint32_t* mpos,
-                               const BitmapDesc* desc, uint2* mtab,
-                               uint32_t* ttab, uint32_t nbitmaps, uint32_t W,
-                               uint32_t NG, cudaStream_t st);
+// Build kernels (thr_build.cu).  Part a: segmented scan of the marker
+// extents into mtab, the subtile table ttab (a build temporary) and the
+// subtile classes with per-bitmap counts of mixed subtiles.  Part b, once the
+// host has placed the mask records: the mask records and final descriptors.
+cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
+                                 const BitmapDesc* desc, uint2* mtab, uint32_t* ttab,
+                                 uint64_t* sdesc, uint32_t* mixed_count,
+                                 uint32_t nbitmaps, uint32_t W, uint32_t NG,
+                                 cudaStream_t st);
+cudaError_t launch_index_build_b(const uint2* mtab, const uint32_t* ttab,
+                                 const BitmapDesc* desc, const uint64_t* mixed_base,
+                                 uint64_t* sdesc, MaskRec* masks, uint32_t nbitmaps,
+                                 uint32_t W, uint32_t NG, cudaStream_t st);
 
 }  // namespace thr
