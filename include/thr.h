@@ -132,6 +132,31 @@ thr_status thr_query_batch(const thr_index *idx, uint32_t nq,
                            uint64_t *out_len, uint32_t flags,
                            void *cuda_stream);
 
+/*
+ * The same query as thr_query, for callers that cannot allocate device
+ * memory while they answer it (the paper has no counterpart: this is a
+ * property of the library).  Examples: a process whose GPU memory is owned
+ * by another allocator that reserved the device up front, or code that must
+ * not risk an allocation failure, or the device synchronisation an
+ * allocation or free can cause, in the middle of its work.  Every scratch
+ * buffer the kernels need lives in one fixed device array of about 8.75 MiB
+ * inside the library, which each GPU that loads the library holds until the
+ * process exits; the call allocates nothing (no cudaMalloc, stream-ordered
+ * or pinned allocation).
+ *   out       device memory only, cap words; the other arguments and the
+ *             result are as for thr_query with THR_OUT_DEVICE
+ * Limits: ceil(r/64) <= 2^20 words (r <= 2^26 rows) and n <= 65536;
+ * larger queries return THR_E_INVAL.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * reuses the same array, so calls whose work overlaps on the GPU (other
+ * streams or host threads) race on it: do not let two such calls run at
+ * the same time.  Synchronous like thr_query.
+ */
+thr_status thr_query_static(const thr_index *idx, const uint32_t *ids, uint32_t n,
+                            uint32_t T, uint64_t *out, uint64_t cap,
+                            uint64_t *out_len, void *cuda_stream);
+
 /* Release an index (NULL-safe); waits for in-flight work on its device. */
 void idx_free(thr_index *idx);
 

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 6: "THR_E_TIMEOUT"}
 
 # every symbol include/thr.h declares
-ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "idx_free",
+ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_free",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -62,6 +62,7 @@ def load():
             lib.idx_build_rle.argtypes = [vp, vp, u32, u64, vp, ctypes.POINTER(vp)]
             lib.thr_query.argtypes = [vp, vp, u32, u32, vp, u64, u64p, u32, vp]
             lib.thr_query_batch.argtypes = [vp, u32, vp, vp, vp, vp, u64, vp, vp, u32, vp]
+            lib.thr_query_static.argtypes = [vp, vp, u32, u32, vp, u64, u64p, vp]
             lib.idx_free.argtypes = [vp]
             lib.idx_free.restype = None
             lib.idx_info.argtypes = [vp, u32p, u64p, u64p]
@@ -71,7 +72,7 @@ def load():
             lib.thr_last_error.restype = ctypes.c_char_p
             lib.thr_last_kernel_ms.argtypes = []
             lib.thr_last_kernel_ms.restype = ctypes.c_double
-            for f in ("idx_build_rle", "thr_query", "thr_query_batch", "idx_info",
+            for f in ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_info",
                       "thr_rle_encode", "thr_rle_validate"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -196,6 +197,22 @@ def thr_query_raw(idx: Index, ids, T: int, out_ptr: int, cap: int, flags: int,
                           ids.size, int(T), ctypes.c_void_p(out_ptr), int(cap),
                           ctypes.byref(n), int(flags), ctypes.c_void_p(_stream(stream)))
     return st, n.value
+
+
+def thr_query_static(idx: Index, ids, T: int, out, stream=None, cap: int | None = None) -> int:
+    """thr_query_static: the query without any allocation (scratch in a fixed
+    device array of the library); `out` must be device memory.  Returns the
+    number of words written."""
+    ids = _u32(ids)
+    n = ctypes.c_uint64(0)
+    size = cap if cap is not None else (out.numel() if hasattr(out, "numel") else out.size)
+    st = load().thr_query_static(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                                 ids.size, int(T), ctypes.c_void_p(_ptr(out)), int(size),
+                                 ctypes.byref(n), ctypes.c_void_p(_stream(stream)))
+    if st == THR_E_NOSPACE:
+        raise ThrError(st, "thr_query_static", f"needs {n.value} words")
+    _check(st, "thr_query_static")
+    return n.value
 
 
 def thr_query_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None):

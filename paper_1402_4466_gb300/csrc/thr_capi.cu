@@ -22,28 +22,10 @@
 #include "../../include/thr.h"
 #include "rle_host.h"
 #include "thr_device.cuh"
+#include "thr_index.h"
 #include "thr_launch.h"
 
 using namespace thr;
-
-struct thr_index {
-    int device = 0;
-    uint32_t nbitmaps = 0;
-    uint64_t r = 0;
-    uint32_t W = 0;   // ceil(r / 64)
-    uint32_t NG = 0;  // ceil(W / 128)
-    uint64_t total_words = 0;
-    uint64_t total_markers = 0;
-    uint64_t* d_words = nullptr;
-    uint2* d_mtab = nullptr;
-    uint64_t* d_sdesc = nullptr;  // NG subtile descriptors per bitmap
-    MaskRec* d_masks = nullptr;   // mask records of the mixed subtiles
-    uint64_t mixed_subtiles = 0;
-    BitmapDesc* d_desc = nullptr;
-    std::vector<BitmapDesc> desc;
-    std::vector<uint64_t> set_rows;
-    int num_sms = 0;
-};
 
 namespace {
 
@@ -265,6 +247,8 @@ bool is_device_ptr(const void* p) {
 }  // namespace
 
 namespace thr {
+thr_status report_error(thr_status st, const char* msg) { return fail(st, "%s", msg); }
+
 const KernelEntry* kernel_table(int* count) {
     static const KernelEntry tab[] = {
         {1, launch_threshold_1, occupancy_threshold_1},

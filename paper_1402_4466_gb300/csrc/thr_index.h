@@ -1,0 +1,33 @@
+// The index object behind the opaque thr_index handle of include/thr.h
+// (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/thr.h"
+#include "thr_device.cuh"
+
+struct thr_index {
+    int device = 0;
+    uint32_t nbitmaps = 0;
+    uint64_t r = 0;
+    uint32_t W = 0;   // ceil(r / 64)
+    uint32_t NG = 0;  // ceil(W / 128)
+    uint64_t total_words = 0;
+    uint64_t total_markers = 0;
+    uint64_t* d_words = nullptr;
+    uint2* d_mtab = nullptr;
+    uint64_t* d_sdesc = nullptr;  // NG subtile descriptors per bitmap
+    thr::MaskRec* d_masks = nullptr;  // mask records of the mixed subtiles
+    uint64_t mixed_subtiles = 0;
+    thr::BitmapDesc* d_desc = nullptr;
+    std::vector<thr::BitmapDesc> desc;
+    std::vector<uint64_t> set_rows;
+    int num_sms = 0;
+};
+
+namespace thr {
+// Records msg as the calling thread's thr_last_error() and returns st.
+thr_status report_error(thr_status st, const char* msg);
+}  // namespace thr
