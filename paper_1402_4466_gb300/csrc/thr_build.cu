@@ -176,10 +176,10 @@ __global__ void k_subtile_class(const uint2* __restrict__ mtab,
 }
 
 // Mask records of the mixed subtiles (layout: MaskRec in thr_device.cuh):
-// literal-word mask, group-start mask (markers starting strictly after the
-// subtile's first word), ones-fill mask, the stream index of the first
-// literal at or after the subtile start (base) and the per-32-word prefix
-// counts.  The literal at subtile word x then sits at stream index
+// literal-word mask, literal-or-group-start mask (groups starting strictly
+// after the subtile's first word), ones-fill mask, the stream index of the
+// first literal at or after the subtile start (base) and the per-32-word
+// prefix counts.  The literal at subtile word x then sits at stream index
 // base + (literal words in [x0, x)) + (group starts in (x0, x]), because every
 // group after the first adds one marker word before its literals.
 __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
@@ -224,15 +224,16 @@ __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
     }
     MaskRec rec;
     uint32_t run = 0;
+    rec.pre = 0;
     for (int w = 0; w < 4; ++w) {
         rec.lm[w] = lm[w];
-        rec.gm[w] = gm[w];
+        rec.cm[w] = lm[w] | gm[w];
         rec.om[w] = om[w];
-        rec.pre[w] = uint16_t(run);
+        rec.pre |= run << (8 * w);
         run += __popc(lm[w]) + __popc(gm[w]);
     }
     rec.base = base;
-    rec.pad = 0;
+    rec.pad[0] = rec.pad[1] = 0;
     const uint64_t idx = mixed_base[b] + (sd >> 19);
     masks[idx] = rec;
     sdesc[i] = (sd & ((1ull << 19) - 1)) | (idx << 19);

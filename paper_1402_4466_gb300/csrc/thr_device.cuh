@@ -49,18 +49,21 @@ constexpr int kWPL = 4;           // consecutive words per lane
 constexpr int kCH = 128;          // input records per warp and chunk
 constexpr int kSMax = 16;         // largest counter width instantiated
 
-// Mask record of a mixed (bitmap, subtile): bit r of lm / gm / om is subtile
-// word x0 + r being a literal / starting a marker group / a ones-fill word;
-// base = stream index (relative to the bitmap's first word) of the first
-// literal at or after x0; pre[w] = literal words + group starts before word
-// 32 w of the subtile (excluding x0 itself).
+// Mask record of a mixed (bitmap, subtile), one 64-byte line.  Bit j of
+// word w of lm / cm / om is subtile word x0 + 32 w + j being a literal /
+// a literal or the start of a marker group / a ones-fill word (a group
+// starts only at a fill word, so a literal never starts one); base = stream
+// index (relative to the bitmap's first word) of the first literal at or
+// after x0; byte w of pre = literal words + group starts before word 32 w
+// (excluding x0, at most 192).  The literal at x0 + 32 w + j then sits at
+// stream index base + pre[w] + popc(cm[w] below bit j).
 struct MaskRec {
     uint32_t lm[4];
-    uint32_t gm[4];
+    uint32_t cm[4];
     uint32_t om[4];
     uint32_t base;
-    uint16_t pre[4];
-    uint32_t pad;
+    uint32_t pre;
+    uint32_t pad[2];
 };
 static_assert(sizeof(MaskRec) == 64, "mask record is one 64-byte line");
 

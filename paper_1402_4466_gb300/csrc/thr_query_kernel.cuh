@@ -16,9 +16,11 @@ constexpr int kRows = kGW / 32;
 // A record is {x, y} = first literal word (one literal run) or mask record
 // index (mixed); {z, w} = stream offset of the bitmap (40 bits) | ones-fill
 // flag << 62 | mixed flag << 63.
+constexpr int kMetaBatch = 32;  // mask records staged per round trip
+
 struct WarpSmem {
     uint4 rec[kCH];
-    uint4 meta[kGroup][4];       // the current group's mask records
+    uint4 meta[kMetaBatch][4];   // mask records of kMetaBatch consecutive inputs
     unsigned long long tw[kGW];  // the subtile's result words, for the scan
 };
 
@@ -35,20 +37,20 @@ constexpr size_t cta_smem_bytes() { return sizeof(CtaSmem); }
 // x0 + 32 r + lane (row r = 0..3).  A literal run is read as four coalesced
 // 256-byte rows.  For a mixed input, word x0 + 32 r + lane is a literal iff
 // bit `lane` of lm[r] of its 64-byte mask record, and sits at stream index
-// base + pre[r] + popc(lm[r] below lane) + popc(gm[r] up to lane); other
-// words are ones (om bit) or zero.  The group's mask records are staged in
+// base + pre[r] + popc(cm[r] below lane); other words are ones (om bit) or
+// zero, and rows without literals or ones are skipped.  The group's mask records are staged in
 // shared memory first (one 16-byte load per lane), then every literal load
 // of the group is issued.
-__device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
-                                             uint32_t r0, uint32_t nrec, uint32_t x0,
-                                             uint32_t x1, uint32_t lane,
-                                             uint64_t (&v)[kGroup][kRows]) {
-    const uint32_t bit = 1u << lane;
-    const uint32_t lt = bit - 1u, le = lt | bit;
-    if (lane < 4 * kGroup) {
-        const uint32_t j = lane >> 2, part = lane & 3;
-        if (r0 + j < nrec) {
-            const uint4 rec = ws.rec[r0 + j];
+// Stage the mask records of inputs m0 .. m0 + kMetaBatch - 1 (lane: 16
+// bytes of 4 records); literal runs and absent ones-fill masks are skipped.
+__device__ __forceinline__ void stage_masks(const QueryParams& p, WarpSmem& ws, uint32_t m0,
+                                           uint32_t nrec, uint32_t lane) {
+    const uint32_t part = lane & 3;
+#pragma unroll
+    for (int k = 0; k < kMetaBatch / 8; ++k) {
+        const uint32_t j = (lane >> 2) + 8 * k;
+        if (m0 + j < nrec) {
+            const uint4 rec = ws.rec[m0 + j];
             if ((rec.w >> 31) && (part != 2 || ((rec.w >> 30) & 1u))) {
                 const uint4* m = reinterpret_cast<const uint4*>(
                     p.masks + ((uint64_t(rec.y) << 32) | rec.x));
@@ -57,6 +59,15 @@ __device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
         }
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
+                                             uint32_t r0, uint32_t nrec, uint32_t x0,
+                                             uint32_t x1, uint32_t lane,
+                                             uint64_t (&v)[kGroup][kRows]) {
+    const uint32_t bit = 1u << lane;
+    const uint32_t lt = bit - 1u;
+    const uint32_t mb = r0 % kMetaBatch;  // the group's first slot in the staged batch
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) {
 #pragma unroll
@@ -71,17 +82,26 @@ __device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
                 if (x0 + 32 * r + lane < x1) v[j][r] = __ldg(src + 32 * r);
             continue;
         }
-        const uint4 lmv = ws.meta[j][0], gmv = ws.meta[j][1], bp = ws.meta[j][3];
-        const uint4 omv = ((rec.w >> 30) & 1u) ? ws.meta[j][2] : make_uint4(0, 0, 0, 0);
+        const uint4 lmv = ws.meta[mb + j][0], cmv = ws.meta[mb + j][1], bp = ws.meta[mb + j][3];
         const uint64_t* src = p.words + ((uint64_t(rec.w & 0xFFu) << 32) | rec.z) + bp.x;
         const uint32_t lm[4] = {lmv.x, lmv.y, lmv.z, lmv.w};
-        const uint32_t gm[4] = {gmv.x, gmv.y, gmv.z, gmv.w};
-        const uint32_t om[4] = {omv.x, omv.y, omv.z, omv.w};
-        const uint32_t pre[4] = {bp.y & 0xFFFFu, bp.y >> 16, bp.z & 0xFFFFu, bp.z >> 16};
+        const uint32_t cm[4] = {cmv.x, cmv.y, cmv.z, cmv.w};
+        if ((rec.w >> 30) & 1u) {  // has ones-fill words in this subtile
+            const uint4 omv = ws.meta[mb + j][2];
+            const uint32_t om[4] = {omv.x, omv.y, omv.z, omv.w};
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const uint32_t off = pre[r] + __popc(lm[r] & lt) + __popc(gm[r] & le);
-            v[j][r] = (lm[r] & bit) ? __ldg(src + off) : ((om[r] & bit) ? ~0ull : 0ull);
+            for (int r = 0; r < kRows; ++r) {
+                if ((lm[r] | om[r]) == 0u) continue;  // the row is all zero fill
+                const uint32_t off = ((bp.y >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
+                v[j][r] = (lm[r] & bit) ? __ldg(src + off) : ((om[r] & bit) ? ~0ull : 0ull);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                if (lm[r] == 0u) continue;  // the row is all zero fill
+                const uint32_t off = ((bp.y >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
+                if (lm[r] & bit) v[j][r] = __ldg(src + off);
+            }
         }
     }
     __syncwarp();
@@ -152,6 +172,10 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
         }
         // 2. the active inputs into the register counters, a group at a time
         for (uint32_t r0 = 0; r0 < nrec; r0 += kGroup) {
+            if (r0 % kMetaBatch == 0) {
+                __syncwarp();
+                stage_masks(p, ws, r0, nrec, lane);
+            }
             uint64_t v[kGroup][kRows];
             decode_group(p, ws, r0, nrec, x0, x1, lane, v);
             if (p.zmode) {  // count the zeros of the active inputs
