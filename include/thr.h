@@ -67,6 +67,16 @@ typedef enum {
 #define THR_POLICY_LEARNED 0x20u /* batch: learned cost-model choice */
 #define THR_POLICY_MASK 0xF0u
 #define THR_PROFILE 0x100u      /* time the query kernel with CUDA events */
+/* Counting kernel of a query (thr_query; thr_query_batch with
+ * THR_POLICY_PLAIN uses it for every query):
+ *   THR_VARIANT_CSA        carry-save bit-sliced counters in registers
+ *                          (default; any n and T)
+ *   THR_VARIANT_SCANCOUNT  ScanCount: one byte counter per row in shared
+ *                          memory per subtile (Sec. 5.1), for very sparse
+ *                          inputs; used when n <= 255, else CSA runs */
+#define THR_VARIANT_CSA 0x000u
+#define THR_VARIANT_SCANCOUNT 0x200u
+#define THR_VARIANT_MASK 0xE00u
 
 /*
  * Build a device-resident index from canonical streams (Sec. 3.1 format

@@ -25,6 +25,7 @@ THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT = 4, 5, 6
 THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
+THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT = 0x000, 0x200
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",

@@ -147,7 +147,7 @@ WidthChoice choose_width(uint32_t n, uint32_t T) {
 // encoded length in *len (also when it exceeds cap).
 thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
                      uint32_t T, uint64_t* dout, uint64_t cap, uint64_t* len,
-                     cudaStream_t st, bool profile) {
+                     cudaStream_t st, bool profile, uint32_t variant) {
     const uint32_t NG = idx->NG;
     // one scratch block: control words | ids | aggregates | prefixes | U
     const size_t o_ids = 256;
@@ -174,6 +174,7 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     CK(cudaMemsetAsync(d_ctl, 0, 64, st), "clear control words");
 
     const WidthChoice wc = choose_width(n, T);
+    const bool scancount = variant == THR_VARIANT_SCANCOUNT && n <= 255;
     QueryParams p{};
     p.words = idx->d_words;
     p.mtab = idx->d_mtab;
@@ -183,7 +184,7 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     p.ids = d_ids;
     p.n = n;
     p.T = T;
-    p.zmode = wc.zmode;
+    p.zmode = scancount ? 0u : wc.zmode;
     p.W = idx->W;
     p.NG = NG;
     p.ntiles = NG;
@@ -193,7 +194,7 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     p.aggs = d_aggs;
     int per_sm = 0;
     TRACE("query n=%u T=%u NG=%u S=%d zmode=%u", n, T, NG, wc.k->S, wc.zmode);
-    CK(wc.k->occupancy(&per_sm), "occupancy query");
+    CK(scancount ? occupancy_scancount(&per_sm) : wc.k->occupancy(&per_sm), "occupancy query");
     const int grid = int(std::min<uint64_t>((NG + kNW - 1) / kNW,
                                             uint64_t(std::max(per_sm, 1)) * idx->num_sms));
     TRACE("pass A grid=%d per_sm=%d", grid, per_sm);
@@ -203,7 +204,9 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
         CK(cudaEventCreate(&ev[1]), "event");
         CK(cudaEventRecord(ev[0], st), "event record");
     }
-    CK(wc.k->launch(p, std::max(grid, 1), st), "launch threshold kernel");
+    CK(scancount ? launch_scancount(p, std::max(grid, 1), st)
+                 : wc.k->launch(p, std::max(grid, 1), st),
+       "launch threshold kernel");
     if (profile) CK(cudaEventRecord(ev[1], st), "event record");
     if (trace_on()) CK(cudaStreamSynchronize(st), "pass A");
     TRACE("pass A done");
@@ -472,9 +475,12 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     if (!idx || !ids || !out_len || (cap > 0 && !out))
         return fail(THR_E_INVAL, "null argument");
     if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
-    if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE))
+    if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK))
         return fail(THR_E_INVAL, "unknown flags");
     const bool profile = flags & THR_PROFILE;
+    const uint32_t variant = flags & THR_VARIANT_MASK;
+    if (variant != THR_VARIANT_CSA && variant != THR_VARIANT_SCANCOUNT)
+        return fail(THR_E_INVAL, "unknown variant");
     for (uint32_t i = 0; i < n; ++i)
         if (ids[i] >= idx->nbitmaps)
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
@@ -483,7 +489,7 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     if (dev_out && cap > 0 && !is_device_ptr(out))
         return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
     if (dev_out) {
-        thr_status s = run_query(idx, ids, n, T, out, cap, out_len, st, profile);
+        thr_status s = run_query(idx, ids, n, T, out, cap, out_len, st, profile, variant);
         if (s == THR_OK && *out_len > cap)
             return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)*out_len);
         return s;
@@ -497,7 +503,7 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
         CK(scr.alloc((void**)&dbuf, sizeof(uint64_t) * std::max<uint64_t>(dcap, 1)),
            "scratch (output)");
         uint64_t len = 0;
-        thr_status s = run_query(idx, ids, n, T, dbuf, dcap, &len, st, profile);
+        thr_status s = run_query(idx, ids, n, T, dbuf, dcap, &len, st, profile, variant);
         if (s != THR_OK) return s;
         *out_len = len;
         if (len > cap)
@@ -526,7 +532,8 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
         uint64_t len = 0;
         thr_status s = thr_query(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
                                  room ? pool + at : nullptr, room, &len,
-                                 flags & (THR_OUT_DEVICE | THR_PROFILE), cuda_stream);
+                                 flags & (THR_OUT_DEVICE | THR_PROFILE | THR_VARIANT_MASK),
+                                 cuda_stream);
         out_off[q] = at;
         out_len[q] = len;
         if (s == THR_E_NOSPACE) {

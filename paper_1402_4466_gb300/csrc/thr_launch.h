@@ -17,6 +17,10 @@ struct KernelEntry {
     OccupancyFn occupancy;
 };
 
+// Pass A with ScanCount counters (thr_scancount.cu): n <= 255, ones only.
+cudaError_t launch_scancount(const QueryParams&, int grid, cudaStream_t);
+cudaError_t occupancy_scancount(int* blocks_per_sm);
+
 // Instantiated counter widths, ascending; a query uses the first S with
 // 2^S > the largest threshold its counters test.
 const KernelEntry* kernel_table(int* count);

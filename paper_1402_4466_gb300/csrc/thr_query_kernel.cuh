@@ -107,19 +107,46 @@ __device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
     __syncwarp();
 }
 
-// One warp computes the 128 result words of subtile [x0, x1); lane owns rows
-// r = 0..3, words x0 + 32 r + lane (zero past x1).
+// Counting policy of the carry-save path: bit-sliced counters in registers
+// (Counters<S>), inputs added four at a time, "count >= thr" compared slice
+// by slice.
 template <int S>
+struct CsaCount {
+    Counters<S> cnt;
+    __device__ __forceinline__ void begin() { cnt.clear(); }
+    __device__ __forceinline__ void add(const uint64_t (&v)[kGroup][kRows], uint32_t) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            cnt.add4(2 * r, uint32_t(v[0][r]), uint32_t(v[1][r]), uint32_t(v[2][r]),
+                     uint32_t(v[3][r]));
+            cnt.add4(2 * r + 1, uint32_t(v[0][r] >> 32), uint32_t(v[1][r] >> 32),
+                     uint32_t(v[2][r] >> 32), uint32_t(v[3][r] >> 32));
+        }
+    }
+    // thr >= 1; flip inverts the result (counting zeros)
+    __device__ __forceinline__ void finish(uint32_t thr, uint32_t flip, uint64_t (&o)[kRows]) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t lo = cnt.ge(2 * r, thr) ^ flip;
+            const uint32_t hi = cnt.ge(2 * r + 1, thr) ^ flip;
+            o[r] = (uint64_t(hi) << 32) | lo;
+        }
+    }
+};
+
+// One warp computes the 128 result words of subtile [x0, x1); lane owns rows
+// r = 0..3, words x0 + 32 r + lane (zero past x1).  Count is the counting
+// policy (carry-save bit slices, or ScanCount counters).
+template <class Count>
 __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSmem& sm,
                                                bool cached, uint32_t x0, uint32_t x1,
-                                               uint32_t lane, WarpSmem& ws,
+                                               uint32_t lane, WarpSmem& ws, Count& count,
                                                uint64_t (&o)[kRows]) {
 #pragma unroll
     for (int q = 0; q < kRows; ++q) o[q] = 0;
     if (x0 >= p.W) return;
     const uint32_t g = x0 / kGW;
-    Counters<S> cnt;
-    cnt.clear();
+    count.begin();
     uint32_t k_ones = 0, d_act = 0;
     const bool one_chunk = p.n <= uint32_t(kCH);
     bool pruned = false;
@@ -170,7 +197,7 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
             const int64_t Tp = int64_t(p.T) - int64_t(k_ones);
             if (Tp <= 0 || Tp > int64_t(d_act)) break;
         }
-        // 2. the active inputs into the register counters, a group at a time
+        // 2. the active inputs into the counters, a group at a time
         for (uint32_t r0 = 0; r0 < nrec; r0 += kGroup) {
             if (r0 % kMetaBatch == 0) {
                 __syncwarp();
@@ -185,13 +212,7 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
                     for (int r = 0; r < kRows; ++r)
                         if (r0 + j < nrec) v[j][r] = ~v[j][r];
             }
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                cnt.add4(2 * r, uint32_t(v[0][r]), uint32_t(v[1][r]),
-                         uint32_t(v[2][r]), uint32_t(v[3][r]));
-                cnt.add4(2 * r + 1, uint32_t(v[0][r] >> 32), uint32_t(v[1][r] >> 32),
-                         uint32_t(v[2][r] >> 32), uint32_t(v[3][r] >> 32));
-            }
+            count.add(v, min(uint32_t(kGroup), nrec - r0));
         }
         __syncwarp();
     }
@@ -202,13 +223,7 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
         for (int r = 0; r < kRows; ++r) o[r] = ~0ull;
     } else if (Tp <= int64_t(d_act)) {
         const uint32_t thr = p.zmode ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
-        const uint32_t flip = p.zmode ? ~0u : 0u;
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const uint32_t lo = cnt.ge(2 * r, thr) ^ flip;
-            const uint32_t hi = cnt.ge(2 * r + 1, thr) ^ flip;
-            o[r] = (uint64_t(hi) << 32) | lo;
-        }
+        count.finish(thr, p.zmode ? ~0u : 0u, o);
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -305,15 +320,13 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
     return L;
 }
 
-// Pass A: each warp of the persistent grid takes every (grid warps)-th
-// 128-word subtile, computes the subtile's result words, stores them in the
-// scratch buffer U (skipped when the subtile holds one fill class only) and
-// stores the subtile's re-encoding aggregate.  No warp ever waits for
-// another.
-template <int S>
-__global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_threshold(const QueryParams p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
+// Pass A driver: each warp of the persistent grid takes every (grid
+// warps)-th 128-word subtile, computes its result words with the counting
+// policy, stores them in the scratch buffer U (skipped when the subtile
+// holds one fill class only) and stores the subtile's re-encoding aggregate.
+// No warp ever waits for another.
+template <class Count>
+__device__ __forceinline__ void pass_a(const QueryParams& p, CtaSmem& sm, Count& count) {
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the query's ids and their stream offsets, once per CTA
     const bool cached = p.n <= uint32_t(kCH);
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_thresh
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint64_t orow[kRows];
-        subtile_result<S>(p, sm, cached, x0, x1, lane, ws, orow);
+        subtile_result(p, sm, cached, x0, x1, lane, ws, count, orow);
         // rows -> 4 consecutive words per lane (the scan's order)
 #pragma unroll
         for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
@@ -347,6 +360,15 @@ __global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_thresh
         }
         if (lane == 0) agg_store_plain(p.aggs + uint64_t(g) * kAggWords, L.A);
     }
+}
+
+// Pass A with the carry-save counters (S-bit saturating bit slices).
+template <int S>
+__global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_threshold(const QueryParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
+    CsaCount<S> count;
+    pass_a(p, sm, count);
 }
 
 }  // namespace thr

@@ -41,8 +41,8 @@ class Pair:
         self.g = thr.idx_build_rle(gw, goff, r)
         self.o = oracle.Index(ostreams, r)
 
-    def check(self, ids, T):
-        got = thr.thr_query(self.g, ids, T)
+    def check(self, ids, T, flags=0):
+        got = thr.thr_query(self.g, ids, T, flags=flags)
         want = self.o.threshold(ids, T)
         if not np.array_equal(got, want):
             gr = oracle.decode(got, self.r) if oracle.validate(got, self.r) == 0 else None
@@ -196,3 +196,40 @@ def test_invalid_arguments():
     with pytest.raises(thr.ThrError) as e:
         thr.thr_query(p.g, [], 1)
     assert e.value.status == thr.THR_E_INVAL
+
+
+# ---- the ScanCount counting kernel (per-row byte counters, Sec. 5.1)
+
+SC = thr.THR_VARIANT_SCANCOUNT
+
+
+def test_scancount_random_tiny_all_thresholds():
+    rng = np.random.default_rng(202)
+    for _ in range(20):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 4096, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        for T in range(0, n + 2):
+            p.check(list(range(n)), T, SC)
+
+
+def test_scancount_several_tiles_and_duplicates():
+    r = (1 << 18) + 37
+    words, _ = synth.many_criteria(12, 24, r)
+    p = Pair(words, r)
+    for T in (1, 2, 3, 5, 12, 24, 25):
+        p.check(list(range(24)), T, SC)
+    rng = np.random.default_rng(12)
+    ids = rng.integers(0, 24, size=200).tolist()  # two chunks, n <= 255
+    for T in (1, 2, 10, 50, 100, 200):
+        p.check(ids, T, SC)
+    ids = rng.integers(0, 24, size=300).tolist()  # n > 255: the carry-save kernel runs
+    p.check(ids, 30, SC)
+
+
+def test_scancount_many_criteria_full_size():
+    r = synth.MANY_R
+    words, _ = synth.many_criteria(0, synth.MANY_N, r)
+    p = Pair(words, r)
+    for T in (2, 16):
+        p.check(list(range(synth.MANY_N)), T, SC)
