@@ -123,6 +123,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=5.0):
+        """Wait until nvidia-smi has printed its first sample."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
     def stop(self):
         if self.proc is None:
             return None
@@ -196,18 +202,19 @@ def run_ours(args):
         out_words[T] = n
         return ev0.elapsed_time(ev1), thr.thr_last_kernel_ms()
 
-    for _ in range(args.warmup):
-        for T in Ts:
-            one_query(T, False)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         uuid = None
-    clocks = ClockSampler(uuid)
+    clocks = ClockSampler(uuid)  # from the warm-up on, so that it has samples under load
+    for _ in range(args.warmup):
+        for T in Ts:
+            one_query(T, False)
+    clocks.wait_first()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     q_ms, k_ms, k_bytes = [], [], []
     for _ in range(args.steps):
         for T in Ts:
@@ -218,7 +225,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
     total_ms = sum(q_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -227,6 +233,48 @@ def run_ours(args):
     nq = len(q_ms) * world
     value = nq / (total_ms / 1e3)
     input_gbs = (in_bytes * nq) / (total_ms / 1e3) / 1e9
+
+    # batched: the step's queries as one thr_query_batch call, replayed as a
+    # CUDA graph, with the launch configuration the autotuner picks; timed on
+    # the host clock around the synchronous call, beside the plain per-query
+    # calls timed the same way (L2 flushed before each call)
+    qs = [(ids, T) for T in Ts]
+    pool = torch.empty(len(Ts) * (W + 1), dtype=torch.int64, device="cuda")
+    tune_best, tune_ms = thr.thr_autotune(idx, qs, reps=3, stream=stream)
+
+    def wall(fn):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t1 = time.perf_counter()
+        fn()
+        return (time.perf_counter() - t1) * 1e3
+
+    def batch_call():
+        thr.thr_query_batch(idx, qs, pool=pool, stream=stream)
+
+    def plain_calls():
+        for T in Ts:
+            thr.thr_query(idx, ids, T, out=dout, stream=stream)
+
+    for _ in range(args.warmup):
+        wall(batch_call)
+        wall(plain_calls)
+    b_ms = [wall(batch_call) for _ in range(args.steps)]
+    binfo = thr.thr_last_batch_info()
+    p_ms = [wall(plain_calls) for _ in range(args.steps)]
+    clk = clocks.stop()
+    batched = {
+        "value": round(len(Ts) * args.steps / (sum(b_ms) / 1e3), 3),
+        "unit": "queries/s",
+        "plain_same_clock": round(len(Ts) * args.steps / (sum(p_ms) / 1e3), 3),
+        "clock": "host wall time around each synchronous call",
+        "launch_config": binfo["config"],
+        "graph_replayed": binfo["graph"] == 1,
+        "pass_a_launches": binfo["launches"],
+        "autotune_ms": [round(t, 4) for t in tune_ms],
+    }
+    batched["speedup_vs_plain"] = round(batched["value"] / batched["plain_same_clock"], 3)
 
     # end to end through the C ABI: host ids in, host result out
     e2e_ms, d2h = [], 0
@@ -278,7 +326,8 @@ def run_ours(args):
                      "traffic": ncu_traffic(), "peak_kind": peak_kind,
                      "kernel": "k_threshold", "bytes_per_launch": int(avg_bytes),
                      "kernel_ms": round(avg_kms, 5)},
-        "gpu_launches": len(q_ms),
+        "batched": batched,
+        "gpu_launches": 3 * len(q_ms),  # passes A, B and C per query
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:

@@ -67,6 +67,7 @@ typedef enum {
 #define THR_POLICY_LEARNED 0x20u /* batch: learned cost-model choice */
 #define THR_POLICY_MASK 0xF0u
 #define THR_PROFILE 0x100u      /* time the query kernel with CUDA events */
+#define THR_NO_GRAPH 0x1000u    /* batch: launch directly, no CUDA graph */
 /* Counting kernel of a query (thr_query; thr_query_batch with
  * THR_POLICY_PLAIN uses it for every query):
  *   THR_VARIANT_CSA        carry-save bit-sliced counters in registers
@@ -191,6 +192,36 @@ thr_status thr_rle_validate(const uint64_t *stream, uint64_t len, uint64_t r);
  * query's stream right before and after the kernel launch); -1 if none.
  */
 double thr_last_kernel_ms(void);
+
+/*
+ * Autotuner of the batched launch.  Runs the sample batch (arguments as for
+ * thr_query_batch; flags: a THR_POLICY_* value and THR_VARIANT_* only) under
+ * each of the 8 launch configurations of pass A, reps times each after one
+ * warm-up run, with L2 flushed before every run, and keeps the fastest for
+ * the batch's shape (several kernel classes or one; mean inputs per query)
+ * in the index: later thr_query_batch calls of that shape use it.  A
+ * configuration is 3 bits: 1 subtile-major work order (queries that share
+ * inputs read them at about the same time; else query-major), 2 merge the
+ * counter widths of a chunk into one launch, 4 split the SMs among launches
+ * that run side by side in proportion to their work.
+ *   times  optional, 8 entries: median host time in ms of each configuration
+ *   best   optional: the configuration kept
+ * Results are identical under every configuration; only the time differs.
+ */
+thr_status thr_autotune(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
+                        const uint32_t *ids, const uint32_t *T, uint32_t flags,
+                        uint32_t reps, void *cuda_stream, double *times, uint32_t *best);
+
+/*
+ * Shape of the last thr_query_batch call on this thread: chunks (groups of
+ * queries whose scratch fits, run one after another), pass-A launches, and
+ * graph = 1 if a cached CUDA graph of the same shape was updated and
+ * replayed, 0 if a new graph was instantiated, -1 if none was used, and the
+ * launch configuration of its first chunk (see thr_autotune).  Any pointer
+ * may be NULL.
+ */
+thr_status thr_last_batch_info(uint32_t *chunks, uint32_t *launches, int32_t *graph,
+                               uint32_t *config);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *thr_last_error(void);

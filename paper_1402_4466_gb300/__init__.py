@@ -25,6 +25,7 @@ THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT = 4, 5, 6
 THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
+THR_NO_GRAPH = 0x1000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT = 0x000, 0x200
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
@@ -33,6 +34,7 @@ STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
 
 # every symbol include/thr.h declares
 ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_free",
+               "thr_last_batch_info", "thr_autotune",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -73,8 +75,12 @@ def load():
             lib.thr_last_error.restype = ctypes.c_char_p
             lib.thr_last_kernel_ms.argtypes = []
             lib.thr_last_kernel_ms.restype = ctypes.c_double
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.thr_last_batch_info.argtypes = [u32p, u32p, i32p, u32p]
+            lib.thr_autotune.argtypes = [vp, u32, vp, vp, vp, u32, u32, vp, vp, u32p]
             for f in ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_info",
-                      "thr_rle_encode", "thr_rle_validate"):
+                      "thr_rle_encode", "thr_rle_validate", "thr_last_batch_info",
+                      "thr_autotune"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -220,11 +226,7 @@ def thr_query_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None)
     """Batch of (ids, T) queries.  Returns (out_off, out_len, pool); with
     pool=None a host pool of the worst-case size is allocated."""
     lib = load()
-    nq = len(queries)
-    id_off = np.zeros(nq + 1, dtype=np.uint32)
-    id_off[1:] = np.cumsum([len(q[0]) for q in queries])
-    ids = _u32(np.concatenate([_u32(q[0]) for q in queries]) if nq else [])
-    T = _u32([q[1] for q in queries])
+    nq, id_off, ids, T = _pack(queries)
     if pool is None:
         pool = np.empty(max(nq * (idx.nwords + 1), 1), dtype=np.uint64)
     if getattr(pool, "is_cuda", False):
@@ -240,6 +242,41 @@ def thr_query_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None)
                                ctypes.c_void_p(out_len.ctypes.data), int(flags),
                                ctypes.c_void_p(_stream(stream))), "thr_query_batch")
     return out_off, out_len, pool
+
+
+def thr_last_batch_info() -> dict:
+    """Shape of this thread's last thr_query_batch call: chunks, pass-A
+    launches, graph (1 cached graph replayed, 0 new graph, -1 no graph)."""
+    c, l, g, k = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_int32(0), ctypes.c_uint32(0)
+    _check(load().thr_last_batch_info(ctypes.byref(c), ctypes.byref(l), ctypes.byref(g),
+                                      ctypes.byref(k)), "thr_last_batch_info")
+    return {"chunks": c.value, "launches": l.value, "graph": g.value, "config": k.value}
+
+
+def _pack(queries):
+    nq = len(queries)
+    id_off = np.zeros(nq + 1, dtype=np.uint32)
+    id_off[1:] = np.cumsum([len(q[0]) for q in queries])
+    ids = _u32(np.concatenate([_u32(q[0]) for q in queries]) if nq else [])
+    T = _u32([q[1] for q in queries])
+    return nq, id_off, ids, T
+
+
+def thr_autotune(idx: Index, queries, flags: int = 0, reps: int = 3, stream=None):
+    """Time the 8 pass-A launch configurations on a sample batch of (ids, T)
+    queries and keep the fastest for its shape in the index.  Returns
+    (best configuration, list of median times in ms)."""
+    nq, id_off, ids, T = _pack(queries)
+    times = np.zeros(8, dtype=np.float64)
+    best = ctypes.c_uint32(0)
+    _check(load().thr_autotune(ctypes.c_void_p(idx.handle), nq,
+                               ctypes.c_void_p(id_off.ctypes.data),
+                               ctypes.c_void_p(ids.ctypes.data if ids.size else 0),
+                               ctypes.c_void_p(T.ctypes.data), int(flags), int(reps),
+                               ctypes.c_void_p(_stream(stream)),
+                               ctypes.c_void_p(times.ctypes.data), ctypes.byref(best)),
+           "thr_autotune")
+    return best.value, times.tolist()
 
 
 def thr_rle_encode(words, r: int) -> np.ndarray:

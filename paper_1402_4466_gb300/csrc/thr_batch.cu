@@ -1,0 +1,373 @@
+// Batches of threshold queries: planning (chunks of queries whose scratch
+// fits, and per chunk one pass-A launch per kernel class), execution on a
+// stream, optionally as a CUDA graph captured per batch shape and replayed.
+//
+// Every query of a batch gets a slot of scratch (its result words and
+// re-encoding aggregates) in its chunk; the chunks run one after the other,
+// the pass-A launches of a chunk side by side.  Pass B of each chunk places
+// the chunk's results in the output pool after those of the earlier chunks,
+// so the results lie in query order without a host round trip.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/thr.h"
+#include "thr_batch.h"
+#include "thr_launch.h"
+
+namespace thr {
+
+namespace {
+
+thr_status cuda_error(cudaError_t e, const char* what) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return report_error(e == cudaErrorMemoryAllocation ? THR_E_NOMEM : THR_E_CUDA, msg);
+}
+
+#define CKB(call, what)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_error(e_, what); \
+    } while (0)
+
+constexpr int kAux = 3;  // side streams for concurrent pass-A launches
+
+// Per host thread: pinned staging, side streams, fork events, the capture
+// stream and the cache of instantiated graphs.
+struct GraphSlot {
+    uint64_t key = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+};
+
+struct ThreadCtx {
+    int device = -1;
+    unsigned char* pin = nullptr;
+    size_t pin_bytes = 0;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t fork[kAux + 1] = {};
+    cudaEvent_t join_in = nullptr;  // orders the capture stream after the caller's
+    cudaStream_t cs = nullptr;      // capture stream
+    GraphSlot graphs[8];
+    uint64_t clock = 0;
+    int per_sm[kNumClasses] = {};  // resident CTAs per SM of each kernel class
+    bool ok = false;
+
+    cudaError_t init(int dev) {
+        if (ok && device == dev) return cudaSuccess;
+        release();
+        cudaError_t e;
+        for (int k = 0; k < kAux; ++k)
+            if ((e = cudaStreamCreateWithFlags(&aux[k], cudaStreamNonBlocking)) != cudaSuccess)
+                return e;
+        for (int k = 0; k <= kAux; ++k)
+            if ((e = cudaEventCreateWithFlags(&fork[k], cudaEventDisableTiming)) != cudaSuccess)
+                return e;
+        if ((e = cudaEventCreateWithFlags(&join_in, cudaEventDisableTiming)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        device = dev;
+        for (int c = 0; c < kNumClasses; ++c) per_sm[c] = 0;
+        ok = true;
+        return cudaSuccess;
+    }
+    void release() {
+        if (!ok) return;
+        for (auto& g : graphs)
+            if (g.exec) {
+                cudaGraphExecDestroy(g.exec);
+                g = GraphSlot{};
+            }
+        for (int k = 0; k < kAux; ++k) cudaStreamDestroy(aux[k]);
+        for (int k = 0; k <= kAux; ++k) cudaEventDestroy(fork[k]);
+        cudaEventDestroy(join_in);
+        cudaStreamDestroy(cs);
+        ok = false;
+    }
+    cudaError_t pinned(size_t bytes, unsigned char** out) {
+        if (pin_bytes < bytes) {
+            if (pin) cudaFreeHost(pin);
+            pin = nullptr;
+            pin_bytes = 0;
+            cudaError_t e = cudaMallocHost(&pin, bytes);
+            if (e != cudaSuccess) return e;
+            pin_bytes = bytes;
+        }
+        *out = pin;
+        return cudaSuccess;
+    }
+    ~ThreadCtx() {
+        // the CUDA runtime may already be shutting down at thread exit;
+        // leave the handles to process teardown then
+        if (pin) cudaFreeHost(pin);
+    }
+};
+thread_local ThreadCtx g_ctx;
+
+size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
+
+uint64_t fnv(uint64_t h, uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+        h ^= (v >> (8 * i)) & 0xFF;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+uint64_t env_u64(const char* name, uint64_t dflt) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    return std::strtoull(v, nullptr, 10);
+}
+
+}  // namespace
+
+thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool, uint64_t cap,
+                     uint64_t* h_off, uint64_t* h_len, uint64_t* total, cudaStream_t st,
+                     const BatchOptions& opt, BatchStats* stats) {
+    const uint32_t nq = in.nq;
+    const uint32_t W = idx->W, NG = idx->NG;
+    CKB(g_ctx.init(idx->device), "per-thread streams");
+
+    // ---- chunking: as many slots per chunk as the scratch budget allows
+    const uint64_t per_slot = scratch_per_slot(W, NG);
+    uint64_t budget = opt.scratch_bytes;
+    if (!budget) {
+        budget = 256ull << 20;  // always granted; more when the device has room
+        if (uint64_t(nq) * per_slot > budget) {
+            size_t free_b = 0, total_b = 0;
+            CKB(cudaMemGetInfo(&free_b, &total_b), "device memory info");
+            budget = std::max<uint64_t>(budget, std::min<uint64_t>(8ull << 30, free_b / 4));
+        }
+    }
+    uint64_t Qmax = std::max<uint64_t>(1, budget / per_slot);
+    Qmax = std::min<uint64_t>(Qmax, (uint64_t(1) << 31) / NG);  // pass C grid, item counters
+    Qmax = std::min<uint64_t>(Qmax, env_u64("THR_MAX_SLOTS", Qmax));
+    Qmax = std::max<uint64_t>(Qmax, 1);
+    Qmax = std::min<uint64_t>(Qmax, nq);
+
+    // ---- per query: kernel class, zero counting; per chunk: launches
+    std::vector<QDesc> qd(nq);
+    std::vector<uint8_t> qcls(nq);
+    for (uint32_t q = 0; q < nq; ++q) {
+        const uint32_t n = in.id_off[q + 1] - in.id_off[q];
+        int cls = 0;
+        uint32_t z = 0;
+        choose_class(n, in.T[q], &cls, &z);
+        const int want = in.cls ? in.cls[q] : -1;
+        if (want == kClassScanCount && n <= 255) {
+            cls = kClassScanCount;
+            z = 0;
+        }
+        qd[q] = QDesc{in.id_off[q], n, in.T[q], z};
+        qcls[q] = uint8_t(cls);
+    }
+    int* per_sm = g_ctx.per_sm;
+    // THR_TUNE_CONFIG=k in the environment forces configuration k (testing)
+    const uint64_t env_cfg = env_u64("THR_TUNE_CONFIG", kTuneCandidates);
+    std::vector<ChunkPlan> chunks;
+    std::vector<Launch> launches;
+    std::vector<uint32_t> lists;
+    lists.reserve(nq);
+    uint64_t key = fnv(14695981039346656037ull, nq > 0 ? 1 : 0);
+    uint32_t first_cfg = 0;
+    for (uint32_t q0 = 0; q0 < nq; q0 += uint32_t(Qmax)) {
+        const uint32_t Q = uint32_t(std::min<uint64_t>(Qmax, nq - q0));
+        ChunkPlan ch{q0, Q, uint32_t(launches.size()), 0};
+        // the chunk's shape and its launch configuration
+        uint32_t present = 0;
+        double sum_n = 0;
+        int widest = -1;
+        for (uint32_t s = 0; s < Q; ++s) {
+            const int c = qcls[q0 + s];
+            present |= 1u << c;
+            sum_n += qd[q0 + s].n;
+            if (c != kClassScanCount) widest = std::max(widest, c);
+        }
+        const bool multi = __builtin_popcount(present) > 1;
+        uint32_t cfg = opt.force_tune >= 0 ? uint32_t(opt.force_tune)
+                                           : tune_lookup(idx, tune_key(multi, sum_n / Q));
+        if (opt.force_tune < 0 && env_cfg < kTuneCandidates) cfg = uint32_t(env_cfg);
+        if (q0 == 0) first_cfg = cfg;
+        if ((cfg & kTuneMerge) && widest >= 0) {
+            for (uint32_t s = 0; s < Q; ++s)
+                if (qcls[q0 + s] != kClassScanCount) qcls[q0 + s] = uint8_t(widest);
+        }
+        double work[kNumClasses] = {};
+        double work_all = 0;
+        for (uint32_t s = 0; s < Q; ++s) {  // cost ~ inputs x counter slices
+            const int c = qcls[q0 + s];
+            const double w = double(qd[q0 + s].n) * (c == kClassScanCount ? 4.0 : 2.0 + c);
+            work[c] += w;
+            work_all += w;
+        }
+        for (int c = 0; c < kNumClasses; ++c) {
+            const uint32_t off = uint32_t(lists.size());
+            for (uint32_t s = 0; s < Q; ++s)
+                if (qcls[q0 + s] == c) lists.push_back(s);
+            const uint32_t cnt = uint32_t(lists.size()) - off;
+            if (!cnt) continue;
+            if (!per_sm[c]) {  // once per thread and device
+                CKB(class_occupancy(c, &per_sm[c]), "occupancy");
+                per_sm[c] = std::max(per_sm[c], 1);
+            }
+            Launch L{c, off, cnt, (cfg & kTuneOrder) ? 1u : 0u, 1};
+            const uint64_t items = uint64_t(cnt) * NG;
+            double ctas = double(per_sm[c]) * idx->num_sms;
+            if ((cfg & kTuneSplit) && work_all > 0) ctas *= work[c] / work_all;
+            L.grid = int(std::max<uint64_t>(
+                1, std::min<uint64_t>((items + kNW - 1) / kNW, uint64_t(ctas + 0.5))));
+            launches.push_back(L);
+            key = fnv(key, uint64_t(c) << 8 | 1);
+        }
+        ch.l1 = uint32_t(launches.size());
+        chunks.push_back(ch);
+        key = fnv(key, 0xC);
+    }
+    if (stats) {
+        stats->chunks = uint32_t(chunks.size());
+        stats->launches = uint32_t(launches.size());
+        stats->slots = uint32_t(Qmax);
+        stats->tune = first_cfg;
+    }
+
+    // ---- device memory: plan (descriptors, ids, lists) | scratch
+    const uint64_t nids = in.id_off[nq];
+    const size_t o_qd = 0;
+    const size_t o_ids = r256(sizeof(QDesc) * nq);
+    const size_t o_lists = o_ids + r256(sizeof(uint32_t) * nids);
+    const size_t plan_bytes = o_lists + r256(sizeof(uint32_t) * lists.size());
+    const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG);
+    const size_t res_bytes = 16 * size_t(nq) + 16;
+    unsigned char* pin = nullptr;
+    CKB(g_ctx.pinned(plan_bytes + r256(res_bytes), &pin), "pinned staging");
+    std::memcpy(pin + o_qd, qd.data(), sizeof(QDesc) * nq);
+    std::memcpy(pin + o_ids, in.ids, sizeof(uint32_t) * nids);
+    std::memcpy(pin + o_lists, lists.data(), sizeof(uint32_t) * lists.size());
+    unsigned long long* h_res = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
+
+    const bool graph = opt.graph && !opt.profile;
+    cudaStream_t xs = graph ? g_ctx.cs : st;  // the stream the work is enqueued on
+    if (graph) {  // the capture stream starts after the caller's earlier work
+        CKB(cudaEventRecord(g_ctx.join_in, st), "order streams");
+        CKB(cudaStreamWaitEvent(xs, g_ctx.join_in, 0), "order streams");
+    }
+    unsigned char* dmem = nullptr;
+    CKB(cudaMallocAsync(reinterpret_cast<void**>(&dmem), plan_bytes + lay.total, xs),
+        "batch scratch");
+    struct Free {
+        unsigned char* p;
+        cudaStream_t s;
+        ~Free() {
+            if (p) cudaFreeAsync(p, s);
+        }
+    } free_guard{dmem, xs};
+    ExecBufs b{};
+    b.qd = reinterpret_cast<const QDesc*>(dmem + o_qd);
+    b.ids = reinterpret_cast<const uint32_t*>(dmem + o_ids);
+    b.lists = reinterpret_cast<const uint32_t*>(dmem + o_lists);
+    b.scratch = dmem + plan_bytes;
+    b.lay = lay;
+    b.out = dpool;
+    b.cap = cap;
+
+    std::vector<cudaEvent_t> tev;
+    PassATimer timer{nullptr};
+    if (opt.profile) {
+        tev.resize(2 * chunks.size());
+        for (auto& e : tev) CKB(cudaEventCreate(&e), "profile events");
+        timer.ev = tev.data();
+    }
+    struct EvFree {
+        std::vector<cudaEvent_t>& v;
+        ~EvFree() {
+            for (auto e : v) cudaEventDestroy(e);
+        }
+    } ev_guard{tev};
+
+    auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dmem, pin, plan_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = enqueue_plan(idx, chunks.data(), uint32_t(chunks.size()), launches.data(), b, s,
+                         g_ctx.aux, kAux, g_ctx.fork, kAux + 1, opt.profile ? &timer : nullptr);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(h_res, b.scratch + lay.res, 16 * size_t(nq), cudaMemcpyDeviceToHost,
+                            s);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, 8,
+                               cudaMemcpyDeviceToHost, s);
+    };
+
+    if (graph) {
+        CKB(cudaStreamBeginCapture(xs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const cudaError_t ee = enqueue(xs);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(xs, &gr);
+        if (ee != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return cuda_error(ee, "enqueue (capture)");
+        }
+        CKB(ec, "end capture");
+        // reuse an executable graph of the same shape (update its parameters)
+        GraphSlot* slot = nullptr;
+        for (auto& g : g_ctx.graphs)
+            if (g.exec && g.key == key) slot = &g;
+        bool ready = false;
+        if (slot) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(slot->exec, gr, &info) == cudaSuccess) {
+                ready = true;
+                if (stats) stats->graph_reused = 1;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(slot->exec);
+                slot->exec = nullptr;
+            }
+        }
+        if (!ready) {
+            if (!slot) {  // least recently used slot
+                slot = &g_ctx.graphs[0];
+                for (auto& g : g_ctx.graphs)
+                    if (!g.exec || g.used < slot->used) slot = &g;
+                if (slot->exec) cudaGraphExecDestroy(slot->exec);
+                slot->exec = nullptr;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&slot->exec, gr, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                slot->exec = nullptr;
+                return cuda_error(ei, "instantiate graph");
+            }
+            slot->key = key;
+            if (stats) stats->graph_reused = 0;
+        }
+        slot->used = ++g_ctx.clock;
+        cudaGraphDestroy(gr);
+        CKB(cudaGraphLaunch(slot->exec, xs), "launch graph");
+    } else {
+        CKB(enqueue(xs), "enqueue");
+    }
+    CKB(cudaStreamSynchronize(xs), "batch");
+    if (opt.profile) {
+        double ms = 0;
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            float t = 0.f;
+            CKB(cudaEventElapsedTime(&t, tev[2 * c], tev[2 * c + 1]), "profile time");
+            ms += t;
+        }
+        if (stats) stats->pass_a_ms = ms;
+    }
+    for (uint32_t q = 0; q < nq; ++q) {
+        h_off[q] = h_res[2 * size_t(q)];
+        h_len[q] = h_res[2 * size_t(q) + 1];
+    }
+    *total = h_res[2 * size_t(nq)];
+    return THR_OK;
+}
+
+}  // namespace thr

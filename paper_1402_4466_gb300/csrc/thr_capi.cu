@@ -23,6 +23,7 @@
 #include "rle_host.h"
 #include "thr_device.cuh"
 #include "thr_index.h"
+#include "thr_batch.h"
 #include "thr_launch.h"
 
 using namespace thr;
@@ -31,6 +32,7 @@ namespace {
 
 thread_local std::string g_err;
 thread_local double g_kernel_ms = -1.0;
+thread_local BatchStats g_last_stats;
 
 // THR_TRACE=1 in the environment: one stderr line per step of a query.
 bool trace_on() {
@@ -71,41 +73,6 @@ thr_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-// Pinned per-thread staging: the query's ids on the way in, the control
-// words (result length) on the way out.  Grows on demand.
-struct Pinned {
-    uint32_t* p = nullptr;
-    size_t bytes = 0;
-    ~Pinned() {
-        if (p) cudaFreeHost(p);
-    }
-};
-thread_local Pinned g_pin;
-
-cudaError_t pinned(size_t bytes, uint32_t** out) {
-    if (g_pin.bytes < bytes) {
-        if (g_pin.p) cudaFreeHost(g_pin.p);
-        g_pin.p = nullptr;
-        g_pin.bytes = 0;
-        cudaError_t e = cudaMallocHost(&g_pin.p, bytes);
-        if (e != cudaSuccess) return e;
-        g_pin.bytes = bytes;
-    }
-    *out = g_pin.p;
-    return cudaSuccess;
-}
-
-size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
-
-int bit_length(uint64_t v) {
-    int n = 0;
-    while (v) {
-        ++n;
-        v >>= 1;
-    }
-    return n;
-}
-
 // RAII for stream-ordered scratch.
 struct Scratch {
     cudaStream_t st;
@@ -121,120 +88,22 @@ struct Scratch {
     }
 };
 
-struct WidthChoice {
-    const KernelEntry* k;
-    uint32_t zmode;
-};
-
-WidthChoice choose_width(uint32_t n, uint32_t T) {
-    int cnt = 0;
-    const KernelEntry* tab = kernel_table(&cnt);
-    // Counting ones needs 2^S > T; counting the zeros of the active inputs
-    // needs 2^S > n - T + 1.  T = 0 and T > n never reach the counters.
-    uint32_t zmode = 0;
-    int need = 1;
-    if (T >= 1 && T <= n) {
-        const int s1 = bit_length(T), s0 = bit_length(uint64_t(n) - T + 1);
-        zmode = s0 < s1 ? 1u : 0u;
-        need = std::min(s1, s0);
-    }
-    for (int i = 0; i < cnt; ++i)
-        if (tab[i].S >= need) return {&tab[i], zmode};
-    return {&tab[cnt - 1], zmode};
-}
-
 // One query, output to a device buffer `dout` of `cap` words.  Returns the
 // encoded length in *len (also when it exceeds cap).
 thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
                      uint32_t T, uint64_t* dout, uint64_t cap, uint64_t* len,
                      cudaStream_t st, bool profile, uint32_t variant) {
-    const uint32_t NG = idx->NG;
-    // one scratch block: control words | ids | aggregates | prefixes | U
-    const size_t o_ids = 256;
-    const size_t o_aggs = o_ids + round256(sizeof(uint32_t) * n);
-    const size_t o_pref = o_aggs + round256(sizeof(uint32_t) * kAggWords * uint64_t(NG));
-    const uint64_t NB = (NG + 255) / 256;  // scan blocks of pass B
-    const size_t o_bagg = o_pref + round256(sizeof(uint32_t) * kAggWords * uint64_t(NG));
-    const size_t o_bpref = o_bagg + round256(sizeof(uint32_t) * kAggWords * NB);
-    const size_t o_U = o_bpref + round256(sizeof(uint32_t) * kAggWords * NB);
-    const size_t total = o_U + sizeof(uint64_t) * uint64_t(NG) * kGW;
-    Scratch scr(st);
-    unsigned char* blk = nullptr;
-    CK(scr.alloc((void**)&blk, total), "query scratch");
-    uint32_t* d_ctl = reinterpret_cast<uint32_t*>(blk);
-    uint32_t* d_ids = reinterpret_cast<uint32_t*>(blk + o_ids);
-    uint32_t* d_aggs = reinterpret_cast<uint32_t*>(blk + o_aggs);
-    uint32_t* d_pref = reinterpret_cast<uint32_t*>(blk + o_pref);
-    uint64_t* d_U = reinterpret_cast<uint64_t*>(blk + o_U);
-    uint32_t* h = nullptr;
-    CK(pinned(64 + sizeof(uint32_t) * size_t(n), &h), "pinned staging");
-    std::memcpy(h + 16, ids, sizeof(uint32_t) * n);
-    CK(cudaMemcpyAsync(d_ids, h + 16, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st),
-       "upload ids");
-    CK(cudaMemsetAsync(d_ctl, 0, 64, st), "clear control words");
-
-    const WidthChoice wc = choose_width(n, T);
-    const bool scancount = variant == THR_VARIANT_SCANCOUNT && n <= 255;
-    QueryParams p{};
-    p.words = idx->d_words;
-    p.mtab = idx->d_mtab;
-    p.sdesc = idx->d_sdesc;
-    p.masks = idx->d_masks;
-    p.desc = idx->d_desc;
-    p.ids = d_ids;
-    p.n = n;
-    p.T = T;
-    p.zmode = scancount ? 0u : wc.zmode;
-    p.W = idx->W;
-    p.NG = NG;
-    p.ntiles = NG;
-    p.ragged = uint32_t(idx->r % 64);
-    p.ctl = d_ctl;
-    p.U = d_U;
-    p.aggs = d_aggs;
-    int per_sm = 0;
-    TRACE("query n=%u T=%u NG=%u S=%d zmode=%u", n, T, NG, wc.k->S, wc.zmode);
-    CK(scancount ? occupancy_scancount(&per_sm) : wc.k->occupancy(&per_sm), "occupancy query");
-    const int grid = int(std::min<uint64_t>((NG + kNW - 1) / kNW,
-                                            uint64_t(std::max(per_sm, 1)) * idx->num_sms));
-    TRACE("pass A grid=%d per_sm=%d", grid, per_sm);
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (profile) {
-        CK(cudaEventCreate(&ev[0]), "event");
-        CK(cudaEventCreate(&ev[1]), "event");
-        CK(cudaEventRecord(ev[0], st), "event record");
-    }
-    CK(scancount ? launch_scancount(p, std::max(grid, 1), st)
-                 : wc.k->launch(p, std::max(grid, 1), st),
-       "launch threshold kernel");
-    if (profile) CK(cudaEventRecord(ev[1], st), "event record");
-    if (trace_on()) CK(cudaStreamSynchronize(st), "pass A");
-    TRACE("pass A done");
-    WriteParams w{};
-    w.U = d_U;
-    w.aggs = d_aggs;
-    w.pref = d_pref;
-    w.bagg = reinterpret_cast<uint32_t*>(blk + o_bagg);
-    w.bpref = reinterpret_cast<uint32_t*>(blk + o_bpref);
-    w.out = dout;
-    w.cap = cap;
-    w.W = idx->W;
-    w.NG = NG;
-    w.ctl = d_ctl;
-    CK(launch_reencode(w, st), "launch re-encoding kernels");
-    if (trace_on()) CK(cudaStreamSynchronize(st), "passes B, C");
-    TRACE("passes B, C done");
-
-    CK(cudaMemcpyAsync(h, d_ctl, 16, cudaMemcpyDeviceToHost, st), "read result length");
-    CK(cudaStreamSynchronize(st), "query");
-    if (profile) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
-        g_kernel_ms = ms;
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-    }
-    *len = uint64_t(h[2]) | (uint64_t(h[3]) << 32);
+    const uint32_t id_off[2] = {0, n};
+    const uint8_t cls = variant == THR_VARIANT_SCANCOUNT ? uint8_t(kClassScanCount) : 0;
+    BatchInput in{1, id_off, ids, &T, &cls};
+    BatchOptions opt;
+    opt.profile = profile;
+    BatchStats stats;
+    uint64_t off = 0, total = 0;
+    TRACE("query n=%u T=%u NG=%u", n, T, idx->NG);
+    thr_status s = run_batch(idx, in, dout, cap, &off, len, &total, st, opt, &stats);
+    if (s != THR_OK) return s;
+    if (profile) g_kernel_ms = stats.pass_a_ms;
     return THR_OK;
 }
 
@@ -271,11 +140,46 @@ const KernelEntry* kernel_table(int* count) {
 }
 }  // namespace thr
 
+// Argument checks shared by thr_query_batch and thr_autotune; fills the
+// kernel class of every query for the policy in flags.
+static thr_status check_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                       const uint32_t* ids, const uint32_t* T, uint32_t flags,
+                       std::vector<uint8_t>* cls) {
+    if (!idx || !id_off || !T) return fail(THR_E_INVAL, "null argument");
+    if (!ids && id_off[nq] > id_off[0]) return fail(THR_E_INVAL, "null ids");
+    if (id_off[0] != 0) return fail(THR_E_INVAL, "id_off[0] must be 0");
+    const uint32_t policy = flags & THR_POLICY_MASK;
+    if (policy != THR_POLICY_PLAIN && policy != THR_POLICY_RULE && policy != THR_POLICY_LEARNED)
+        return fail(THR_E_INVAL, "unknown policy");
+    const uint32_t variant = flags & THR_VARIANT_MASK;
+    if (variant != THR_VARIANT_CSA && variant != THR_VARIANT_SCANCOUNT)
+        return fail(THR_E_INVAL, "unknown variant");
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
+        const uint32_t n = id_off[q + 1] - id_off[q];
+        if (n == 0 || n > 65536)
+            return fail(THR_E_INVAL, "query %u: n must be in 1..65536", q);
+    }
+    for (uint64_t i = 0; i < id_off[nq]; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    return choose_variants(idx, nq, id_off, ids, T, policy, variant, cls);
+}
+
 extern "C" {
 
 const char* thr_last_error(void) { return g_err.c_str(); }
 
 double thr_last_kernel_ms(void) { return g_kernel_ms; }
+
+thr_status thr_last_batch_info(uint32_t* chunks, uint32_t* launches, int32_t* graph,
+                               uint32_t* config) {
+    if (chunks) *chunks = g_last_stats.chunks;
+    if (launches) *launches = g_last_stats.launches;
+    if (graph) *graph = g_last_stats.graph_reused;
+    if (config) *config = g_last_stats.tune;
+    return THR_OK;
+}
 
 thr_status thr_rle_encode(const uint64_t* words, uint64_t nwords, uint64_t r,
                           uint64_t* out, uint64_t cap, uint64_t* out_len) {
@@ -515,6 +419,19 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     return THR_OK;
 }
 
+thr_status thr_autotune(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                        const uint32_t* ids, const uint32_t* T, uint32_t flags, uint32_t reps,
+                        void* cuda_stream, double* times, uint32_t* best) {
+    if (nq == 0) return fail(THR_E_INVAL, "empty sample batch");
+    if (reps == 0) return fail(THR_E_INVAL, "reps must be at least 1");
+    if (flags & ~(THR_POLICY_MASK | THR_VARIANT_MASK)) return fail(THR_E_INVAL, "unknown flags");
+    std::vector<uint8_t> cls;
+    thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &cls);
+    if (ps != THR_OK) return ps;
+    BatchInput in{nq, id_off, ids, T, cls.data()};
+    return autotune(idx, in, (cudaStream_t)cuda_stream, reps, times, best);
+}
+
 thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint64_t* pool,
                            uint64_t pool_cap, uint64_t* out_off, uint64_t* out_len,
@@ -522,28 +439,55 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
     if (!idx || !id_off || !T || !out_off || !out_len || (pool_cap > 0 && !pool))
         return fail(THR_E_INVAL, "null argument");
     if (nq == 0) return THR_OK;
-    if (!ids && id_off[nq] > 0) return fail(THR_E_INVAL, "null ids");
-    for (uint32_t q = 0; q < nq; ++q)
-        if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
-    uint64_t at = 0;
-    bool nospace = false;
-    for (uint32_t q = 0; q < nq; ++q) {
-        const uint64_t room = at < pool_cap ? pool_cap - at : 0;
-        uint64_t len = 0;
-        thr_status s = thr_query(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
-                                 room ? pool + at : nullptr, room, &len,
-                                 flags & (THR_OUT_DEVICE | THR_PROFILE | THR_VARIANT_MASK),
-                                 cuda_stream);
-        out_off[q] = at;
-        out_len[q] = len;
-        if (s == THR_E_NOSPACE) {
-            nospace = true;
-        } else if (s != THR_OK) {
-            return s;
+    if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK |
+                  THR_NO_GRAPH))
+        return fail(THR_E_INVAL, "unknown flags");
+    std::vector<uint8_t> cls;
+    thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &cls);
+    if (ps != THR_OK) return ps;
+    BatchInput in{nq, id_off, ids, T, cls.data()};
+    BatchOptions opt;
+    opt.graph = !(flags & THR_NO_GRAPH);
+    opt.profile = flags & THR_PROFILE;
+    BatchStats stats;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint64_t total = 0;
+    if (flags & THR_OUT_DEVICE) {
+        if (pool_cap > 0 && !is_device_ptr(pool))
+            return fail(THR_E_INVAL, "THR_OUT_DEVICE given but pool is not device memory");
+        thr_status s = run_batch(idx, in, pool, pool_cap, out_off, out_len, &total, st, opt,
+                                 &stats);
+        if (s != THR_OK) return s;
+    } else {
+        // host pool: results go to a device staging pool first; if they do
+        // not fit there but fit the caller's pool, run again with room
+        uint64_t dcap = std::min<uint64_t>(pool_cap, uint64_t(nq) * (uint64_t(idx->W) + 1));
+        dcap = std::min<uint64_t>(dcap, uint64_t(1) << 27);
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            Scratch scr(st);
+            uint64_t* dbuf = nullptr;
+            CK(scr.alloc((void**)&dbuf, sizeof(uint64_t) * std::max<uint64_t>(dcap, 1)),
+               "scratch (output pool)");
+            thr_status s = run_batch(idx, in, dbuf, dcap, out_off, out_len, &total, st, opt,
+                                     &stats);
+            if (s != THR_OK) return s;
+            if (total > dcap && total <= pool_cap) {
+                dcap = total;
+                continue;
+            }
+            if (total <= pool_cap && total > 0) {
+                CK(cudaMemcpyAsync(pool, dbuf, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost,
+                                   st),
+                   "copy results");
+                CK(cudaStreamSynchronize(st), "copy results");
+            }
+            break;
         }
-        at += len;
     }
-    if (nospace) return fail(THR_E_NOSPACE, "pool needs %llu words", (unsigned long long)at);
+    if (opt.profile) g_kernel_ms = stats.pass_a_ms;
+    g_last_stats = stats;
+    if (total > pool_cap)
+        return fail(THR_E_NOSPACE, "pool needs %llu words", (unsigned long long)total);
     return THR_OK;
 }
 

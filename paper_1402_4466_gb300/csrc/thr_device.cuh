@@ -7,33 +7,28 @@
 //          index of every marker word, the uncompressed word where its group
 //          starts and its fill bit; the extra entry is {len, W}.  ustart is
 //          the segmented exclusive scan of F + L over the marker words
-//          (kernel k_marker_scan), so F and L of marker m follow from the
-//          entries m and m + 1: L = pos' - pos - 1, F = ustart' - ustart - L.
-//   ttab   per bitmap NG + 1 uint32 (NG = ceil(W / 128)): ttab[g] is the
-//          marker whose group contains uncompressed word 128 g; ttab[NG] =
-//          nmark.  A 128-word subtile g overlaps the markers
-//          ttab[g] .. ttab[g + 1] (the last one only if it starts before the
-//          subtile ends).
+//          (kernel k_marker_scan).
+//   sdesc  per bitmap and 128-word subtile one uint64 descriptor: the class
+//          of the bitmap over the subtile (zero fill, ones fill, one literal
+//          run, mixed) and, for a literal run, the stream index of its first
+//          literal, for a mixed subtile the index of its mask record.
+//   masks  one 64-byte MaskRec per mixed (bitmap, subtile).
 //
-// Query kernel (k_threshold<S>): a persistent grid; each CTA takes 512-word
-// tiles in order from an atomic counter.  Per 128-word subtile one warp
-//   1. looks up, lane per input, which markers cover the subtile and
-//      classifies the input there as a fill of zeros, a fill of ones (k of
-//      them), one literal run, or mixed; this is the run-aware pruning of the
-//      RBMrg/EWAH cases of Sec. 6.4: T <= k gives ones, T > k + d zeros
-//      (d = inputs with literals), else T' = T - k over the d active inputs;
-//   2. decodes the active inputs (lane owns 4 consecutive words) and adds
-//      them into bit-sliced counters with LOP3 full adders (carry-save,
-//      Sec. 5.3.1 mentions carry-save and sideways-sum circuits as cheaper
-//      ways to form the Hamming weight than BSTM's ripple); counters
-//      saturate at 2^S (sticky bit) since only "count >= T'" matters, and
-//      when T' is close to d the zeros are counted instead (S bits then
-//      bound d - T' + 1);
-//   3. compares the bit slices with T' most significant slice first (the
-//      O'Neil-Quass comparison BSTM uses, Algorithm 2).
-// The CTA then re-encodes its 512 result words canonically: word classes,
-// head/literal scans, and a decoupled look-back over the tiles before it
-// (bounded spin) give every marker and literal its output position.
+// A query (or a batch of them) runs in three passes:
+//   A  k_threshold<S> / k_scancount: persistent grid; a warp takes a work
+//      item (query, m consecutive subtiles) at a time and, per subtile,
+//      classifies the query's inputs from sdesc (run-aware pruning of
+//      Sec. 6.4: with k ones fills and d inputs holding literals, T <= k
+//      gives ones, T > k + d zeros, else T' = T - k over the d inputs),
+//      decodes the active inputs, counts per row (carry-save bit slices with
+//      LOP3 full adders, or ScanCount byte counters), compares with T', and
+//      stores the subtile's result words (only if they are not one fill)
+//      and its re-encoding aggregate.
+//   B  k_scan_aggs: per query an ordered scan of the aggregates, then a scan
+//      of the result lengths over the queries of the chunk that places each
+//      result in the output pool and writes its final marker.
+//   C  k_write_out: every literal and every marker of a group that ends
+//      inside a subtile goes to its place.
 #pragma once
 
 #include <cstdint>
@@ -85,38 +80,54 @@ struct RangeAgg {
 // Aggregates and prefixes are stored as kAggWords uint32 per subtile.
 constexpr int kAggWords = 8;
 
-struct QueryParams {
+// One query of a batch.  zmode 1: count the zeros of the active inputs.
+struct QDesc {
+    uint32_t ids_off;  // first id in the batch's id array
+    uint32_t n;
+    uint32_t T;
+    uint32_t zmode;
+};
+
+// Pass A of one launch: the queries (slots of the chunk) in list[0..nlist),
+// one work item per (query, subtile), query-major (order 0) or subtile-major
+// (order 1).
+struct PassAParams {
     const uint64_t* words;
-    const uint2* mtab;
     const uint64_t* sdesc;  // subtile descriptors, NG per bitmap
     const MaskRec* masks;   // mask records of the mixed subtiles
     const BitmapDesc* desc;
-    const uint32_t* ids;  // device copy of the query's ids
-    uint32_t n;
-    uint32_t T;
-    uint32_t zmode;   // 1: count zeros among the active inputs
+    const QDesc* qd;        // the chunk's queries, by slot
+    const uint32_t* ids;    // every id of the batch
+    const uint32_t* list;   // slots taken by this launch
+    uint32_t nlist;
+    uint32_t order;   // 0 query-major, 1 subtile-major
     uint32_t W;       // uncompressed words
     uint32_t NG;      // subtiles
-    uint32_t ntiles;  // subtiles (= NG)
     uint32_t ragged;  // r % 64
-    uint32_t spin_limit;
-    uint32_t* ctl;     // [0] subtile counter (zeroed before the launch)
-    uint64_t* U;       // scratch: W result words (only non-uniform subtiles stored)
-    uint32_t* aggs;    // scratch: per subtile re-encoding aggregate
+    uint64_t* U;      // scratch: slot s at U + s NG 128 (only non-uniform subtiles stored)
+    uint32_t* aggs;   // scratch: slot s, subtile g at aggs + (s NG + g) kAggWords
 };
 
-// Passes B and C of the re-encoding (thr_reencode.cu).
+// Passes B and C of the re-encoding (thr_reencode.cu), over the Q slots of
+// one chunk; slot s holds query q0 + s of the batch.
 struct WriteParams {
     const uint64_t* U;
     const uint32_t* aggs;
-    uint32_t* pref;    // per subtile: prefix within its scan block (pass B)
-    uint32_t* bagg;    // per scan block: total
-    uint32_t* bpref;   // per scan block: prefix before it
-    uint64_t* out;     // device output buffer
-    uint64_t cap;
+    uint32_t* pref;     // per (slot, subtile): prefix within its scan block
+    uint32_t* bagg;     // per (slot, scan block): total
+    uint32_t* bpref;    // per (slot, scan block): prefix before it
+    uint32_t* full;     // per slot: aggregate of the whole result
+    uint32_t* tick;     // per slot: pass B ticket (returns to 0)
+    uint32_t* gtick;    // chunk ticket (returns to 0)
+    unsigned long long* base;  // output words placed by earlier chunks
+    unsigned long long* res;   // per query of the batch: {offset, length}
+    uint64_t* out;      // output pool
+    uint64_t cap;       // its capacity in words
     uint32_t W;
     uint32_t NG;
-    uint32_t* ctl;     // [2..3] encoded length (pass B), [4] pass B ticket
+    uint32_t NB;        // scan blocks per slot
+    uint32_t Q;         // slots in the chunk
+    uint32_t q0;        // first query of the chunk
 };
 cudaError_t launch_reencode(const WriteParams& w, cudaStream_t st);
 

@@ -1,0 +1,159 @@
+// Enqueueing a launch plan: the three passes of every chunk of a batch.
+#include "thr_exec.h"
+
+#include <algorithm>
+
+#include "thr_launch.h"
+
+namespace thr {
+
+namespace {
+
+size_t r256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int bits_of(uint64_t v) {
+    int n = 0;
+    while (v) {
+        ++n;
+        v >>= 1;
+    }
+    return n;
+}
+
+cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t st) {
+    if (cls == kClassScanCount) return launch_scancount(p, grid, st);
+    int cnt = 0;
+    const KernelEntry* tab = kernel_table(&cnt);
+    if (cls < 0 || cls >= cnt) return cudaErrorInvalidValue;
+    return tab[cls].launch(p, grid, st);
+}
+
+}  // namespace
+
+uint32_t scan_blocks(uint32_t NG) { return (NG + 255) / 256; }
+
+uint64_t scratch_per_slot(uint32_t W, uint32_t NG) {
+    const uint64_t NB = scan_blocks(NG);
+    return 4 + 32 + 2 * 32 * NB + 2 * 32 * uint64_t(NG) + 8 * uint64_t(NG) * kGW;
+}
+
+ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG) {
+    const uint64_t NB = scan_blocks(NG);
+    const size_t agg = sizeof(uint32_t) * kAggWords;
+    ScratchLayout l{};
+    l.gtick = 0;
+    l.base = 8;
+    l.tick = 256;
+    l.res = l.tick + r256(4 * Q);
+    l.full = l.res + r256(16 * nq);
+    l.bagg = l.full + r256(agg * Q);
+    l.bpref = l.bagg + r256(agg * Q * NB);
+    l.aggs = l.bpref + r256(agg * Q * NB);
+    l.pref = l.aggs + r256(agg * Q * NG);
+    l.U = l.pref + r256(agg * Q * NG);
+    l.total = l.U + r256(8 * Q * uint64_t(NG) * kGW);
+    return l;
+}
+
+void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode) {
+    int cnt = 0;
+    const KernelEntry* tab = kernel_table(&cnt);
+    uint32_t z = 0;
+    int need = 1;
+    if (T >= 1 && T <= n) {  // T = 0 and T > n never reach the counters
+        const int s1 = bits_of(T), s0 = bits_of(uint64_t(n) - T + 1);
+        z = s0 < s1 ? 1u : 0u;
+        need = std::min(s1, s0);
+    }
+    int c = cnt - 1;
+    for (int i = 0; i < cnt; ++i)
+        if (tab[i].S >= need) {
+            c = i;
+            break;
+        }
+    *cls = c;
+    *zmode = z;
+}
+
+cudaError_t class_occupancy(int cls, int* per_sm) {
+    if (cls == kClassScanCount) return occupancy_scancount(per_sm);
+    int cnt = 0;
+    const KernelEntry* tab = kernel_table(&cnt);
+    if (cls < 0 || cls >= cnt) return cudaErrorInvalidValue;
+    return tab[cls].occupancy(per_sm);
+}
+
+cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,
+                         const Launch* launches, const ExecBufs& b, cudaStream_t st,
+                         cudaStream_t* aux, int naux, cudaEvent_t* fork_ev, int nfork_ev,
+                         const PassATimer* timer) {
+    const ScratchLayout& l = b.lay;
+    unsigned char* s = b.scratch;
+    // control words: chunk ticket, running output offset, slot tickets
+    cudaError_t e = cudaMemsetAsync(s, 0, l.res, st);
+    if (e != cudaSuccess) return e;
+    const uint32_t NG = idx->NG;
+    PassAParams p{};
+    p.words = idx->d_words;
+    p.sdesc = idx->d_sdesc;
+    p.masks = idx->d_masks;
+    p.desc = idx->d_desc;
+    p.ids = b.ids;
+    p.W = idx->W;
+    p.NG = NG;
+    p.ragged = uint32_t(idx->r % 64);
+    p.U = reinterpret_cast<uint64_t*>(s + l.U);
+    p.aggs = reinterpret_cast<uint32_t*>(s + l.aggs);
+    WriteParams w{};
+    w.U = p.U;
+    w.aggs = p.aggs;
+    w.pref = reinterpret_cast<uint32_t*>(s + l.pref);
+    w.bagg = reinterpret_cast<uint32_t*>(s + l.bagg);
+    w.bpref = reinterpret_cast<uint32_t*>(s + l.bpref);
+    w.full = reinterpret_cast<uint32_t*>(s + l.full);
+    w.tick = reinterpret_cast<uint32_t*>(s + l.tick);
+    w.gtick = reinterpret_cast<uint32_t*>(s + l.gtick);
+    w.base = reinterpret_cast<unsigned long long*>(s + l.base);
+    w.res = reinterpret_cast<unsigned long long*>(s + l.res);
+    w.out = b.out;
+    w.cap = b.cap;
+    w.W = idx->W;
+    w.NG = NG;
+    w.NB = scan_blocks(NG);
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        const ChunkPlan& ch = chunks[c];
+        p.qd = b.qd + ch.q0;
+        const uint32_t nl = ch.l1 - ch.l0;
+        // several launches run side by side on the aux streams
+        const int nside = std::min<int>(int(nl) - 1, std::min(naux, nfork_ev - 1));
+        if (timer && timer->ev && (e = cudaEventRecord(timer->ev[2 * c], st)) != cudaSuccess)
+            return e;
+        if (nside > 0) {
+            if ((e = cudaEventRecord(fork_ev[0], st)) != cudaSuccess) return e;
+            for (int k = 0; k < nside; ++k)
+                if ((e = cudaStreamWaitEvent(aux[k], fork_ev[0], 0)) != cudaSuccess) return e;
+        }
+        for (uint32_t i = 0; i < nl; ++i) {
+            const Launch& L = launches[ch.l0 + i];
+            p.list = b.lists + L.list_off;
+            p.nlist = L.nlist;
+            p.order = L.order;
+            const int slot = nside > 0 ? int(i % uint32_t(nside + 1)) : 0;
+            cudaStream_t ls = slot == 0 ? st : aux[slot - 1];
+            if ((e = launch_class(L.cls, p, std::max(L.grid, 1), ls)) != cudaSuccess) return e;
+        }
+        for (int k = 0; k < nside; ++k) {
+            if ((e = cudaEventRecord(fork_ev[1 + k], aux[k])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, fork_ev[1 + k], 0)) != cudaSuccess) return e;
+        }
+        if (timer && timer->ev &&
+            (e = cudaEventRecord(timer->ev[2 * c + 1], st)) != cudaSuccess)
+            return e;
+        w.Q = ch.Q;
+        w.q0 = ch.q0;
+        if ((e = launch_reencode(w, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace thr

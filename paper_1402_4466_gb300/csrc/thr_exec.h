@@ -1,0 +1,81 @@
+// Host side of query execution: the launch plan of a batch of queries and
+// the code that enqueues it on a stream (thr_exec.cu).  thr_query,
+// thr_query_batch and thr_query_static all go through enqueue_plan.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "thr_device.cuh"
+#include "thr_index.h"
+
+namespace thr {
+
+// Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
+// kernel_table()[c].S, kClassScanCount the ScanCount kernel.
+constexpr int kNumWidths = 11;
+constexpr int kClassScanCount = kNumWidths;
+constexpr int kNumClasses = kNumWidths + 1;
+
+// One pass-A launch: the slots list[list_off .. list_off + nlist) of its
+// chunk, work items in `order` (0 query-major, 1 subtile-major), `grid` CTAs.
+struct Launch {
+    int cls;
+    uint32_t list_off;
+    uint32_t nlist;
+    uint32_t order;
+    int grid;
+};
+
+// A chunk: queries q0 .. q0 + Q - 1 of the batch in slots 0 .. Q - 1, pass-A
+// launches launches[l0 .. l1).
+struct ChunkPlan {
+    uint32_t q0, Q;
+    uint32_t l0, l1;
+};
+
+// Byte offsets of the scratch regions for chunks of at most Q slots.
+struct ScratchLayout {
+    size_t gtick, base, tick, res, full, bagg, bpref, aggs, pref, U, total;
+};
+ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG);
+// Scratch bytes per slot (everything that grows with Q).
+uint64_t scratch_per_slot(uint32_t W, uint32_t NG);
+uint32_t scan_blocks(uint32_t NG);
+
+// Device pointers of one execution.
+struct ExecBufs {
+    const QDesc* qd;        // nq descriptors
+    const uint32_t* ids;    // every id
+    const uint32_t* lists;  // slot lists of all launches
+    unsigned char* scratch; // ScratchLayout of the largest chunk
+    ScratchLayout lay;
+    uint64_t* out;          // output pool
+    uint64_t cap;
+};
+
+// Times of the pass-A launches (THR_PROFILE): an event pair per chunk.
+struct PassATimer {
+    cudaEvent_t* ev;  // 2 per chunk, or null
+};
+
+// Enqueue the whole plan on st: clear the control words, then per chunk its
+// pass-A launches (forked onto the aux streams when there are several),
+// pass B and pass C.  Results: res (offset, length per query) and base
+// (total words) in scratch.  aux: naux streams for the forks (may be 0).
+cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,
+                         const Launch* launches, const ExecBufs& b, cudaStream_t st,
+                         cudaStream_t* aux, int naux, cudaEvent_t* fork_ev, int nfork_ev,
+                         const PassATimer* timer);
+
+// Counter width and zero counting for a query of n inputs and threshold T:
+// counting ones needs 2^S > T, counting the zeros of the active inputs
+// 2^S > n - T + 1; the class is the first instantiated width that fits.
+void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode);
+
+// CTAs per SM of a class's kernel at full occupancy.
+cudaError_t class_occupancy(int cls, int* per_sm);
+
+}  // namespace thr

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/thr.h"
@@ -25,6 +27,9 @@ struct thr_index {
     std::vector<thr::BitmapDesc> desc;
     std::vector<uint64_t> set_rows;
     int num_sms = 0;
+    // pass-A launch configurations chosen by thr_autotune, per batch shape
+    mutable std::mutex tune_mu;
+    mutable std::map<uint32_t, uint32_t> tune;
 };
 
 namespace thr {

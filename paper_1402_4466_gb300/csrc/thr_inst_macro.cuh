@@ -13,7 +13,7 @@
             int(cta_smem_bytes()));                                        \
         return once;                                                          \
     }                                                                         \
-    cudaError_t launch_threshold_##S(const QueryParams& p, int grid,          \
+    cudaError_t launch_threshold_##S(const PassAParams& p, int grid,          \
                                      cudaStream_t st) {                       \
         cudaError_t e = prepare_threshold_##S();                              \
         if (e != cudaSuccess) return e;                                       \

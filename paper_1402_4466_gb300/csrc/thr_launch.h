@@ -8,7 +8,7 @@
 
 namespace thr {
 
-using LaunchFn = cudaError_t (*)(const QueryParams&, int grid, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const PassAParams&, int grid, cudaStream_t);
 using OccupancyFn = cudaError_t (*)(int* blocks_per_sm);
 
 struct KernelEntry {
@@ -18,7 +18,7 @@ struct KernelEntry {
 };
 
 // Pass A with ScanCount counters (thr_scancount.cu): n <= 255, ones only.
-cudaError_t launch_scancount(const QueryParams&, int grid, cudaStream_t);
+cudaError_t launch_scancount(const PassAParams&, int grid, cudaStream_t);
 cudaError_t occupancy_scancount(int* blocks_per_sm);
 
 // Instantiated counter widths, ascending; a query uses the first S with
@@ -26,7 +26,7 @@ cudaError_t occupancy_scancount(int* blocks_per_sm);
 const KernelEntry* kernel_table(int* count);
 
 #define THR_DECLARE_WIDTH(S)                                            \
-    cudaError_t launch_threshold_##S(const QueryParams&, int, cudaStream_t); \
+    cudaError_t launch_threshold_##S(const PassAParams&, int, cudaStream_t); \
     cudaError_t occupancy_threshold_##S(int*);
 
 THR_DECLARE_WIDTH(1)

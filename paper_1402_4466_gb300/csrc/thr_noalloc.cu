@@ -23,25 +23,20 @@
 #include <mutex>
 
 #include "thr_index.h"
-#include "thr_launch.h"
+#include "thr_exec.h"
 
 namespace thr {
 namespace {
 
-constexpr uint64_t kStaticMaxWords = 1ull << 20;              // r <= 2^26 rows
-constexpr uint64_t kStaticMaxSubtiles = kStaticMaxWords / kGW;
+constexpr uint64_t kStaticMaxWords = 1ull << 20;  // r <= 2^26 rows
 constexpr uint64_t kStaticMaxIds = 65536;
-constexpr uint64_t kStaticBlocks = (kStaticMaxSubtiles + 255) / 256;
-
-// fixed layout: control | ids | aggregates | prefixes | block totals |
-// block prefixes | result words
-constexpr uint64_t kOffIds = 256;
-constexpr uint64_t kOffAggs = kOffIds + 4 * kStaticMaxIds;
-constexpr uint64_t kOffPref = kOffAggs + 4 * kAggWords * kStaticMaxSubtiles;
-constexpr uint64_t kOffBagg = kOffPref + 4 * kAggWords * kStaticMaxSubtiles;
-constexpr uint64_t kOffBpref = kOffBagg + 4 * kAggWords * kStaticBlocks;
-constexpr uint64_t kOffU = kOffBpref + 4 * kAggWords * kStaticBlocks;
-constexpr uint64_t kStaticBytes = kOffU + 8 * kStaticMaxSubtiles * kGW;  // about 8.75 MiB
+// fixed layout: query descriptor | slot list | ids | scratch of one slot
+// (control words, aggregates, prefixes, result words: about 8.5 MiB at the
+// largest r)
+constexpr uint64_t kOffList = 256;
+constexpr uint64_t kOffIds = 512;
+constexpr uint64_t kOffScratch = kOffIds + 4 * kStaticMaxIds;
+constexpr uint64_t kStaticBytes = kOffScratch + 9ull * 1024 * 1024;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticBytes];
 
@@ -62,15 +57,6 @@ cudaError_t scratch_address(int dev, unsigned char** out) {
     }
     *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
     return cudaSuccess;
-}
-
-int bits_needed(uint64_t v) {
-    int n = 0;
-    while (v) {
-        ++n;
-        v >>= 1;
-    }
-    return n;
 }
 
 thr_status cuda_error(cudaError_t e, const char* what) {
@@ -116,70 +102,45 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     }
     unsigned char* blk = nullptr;
     if ((e = scratch_address(dev, &blk)) != cudaSuccess) return cuda_error(e, "scratch address");
+    const ScratchLayout lay = scratch_layout(1, 1, idx->W, idx->NG);
+    if (kOffScratch + lay.total > kStaticBytes)
+        return report_error(THR_E_INVAL, "static scratch too small for this index");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    uint32_t* d_ctl = reinterpret_cast<uint32_t*>(blk);
-    uint32_t* d_ids = reinterpret_cast<uint32_t*>(blk + kOffIds);
-    // the control words (work counter, pass B ticket) must start at zero
-    if ((e = cudaMemsetAsync(d_ctl, 0, 64, st)) != cudaSuccess) return cuda_error(e, "memset");
-    if ((e = cudaMemcpyAsync(d_ids, ids, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-        return cuda_error(e, "upload ids");
-
-    int cnt = 0;
-    const KernelEntry* tab = kernel_table(&cnt);
+    int cls = 0;
     uint32_t zmode = 0;
-    int need = 1;
-    if (T >= 1 && T <= n) {
-        const int s1 = bits_needed(T), s0 = bits_needed(uint64_t(n) - T + 1);
-        zmode = s0 < s1 ? 1u : 0u;
-        need = std::min(s1, s0);
-    }
-    const KernelEntry* k = &tab[cnt - 1];
-    for (int i = 0; i < cnt; ++i)
-        if (tab[i].S >= need) {
-            k = &tab[i];
-            break;
-        }
-    QueryParams p{};
-    p.words = idx->d_words;
-    p.mtab = idx->d_mtab;
-    p.sdesc = idx->d_sdesc;
-    p.masks = idx->d_masks;
-    p.desc = idx->d_desc;
-    p.ids = d_ids;
-    p.n = n;
-    p.T = T;
-    p.zmode = zmode;
-    p.W = idx->W;
-    p.NG = idx->NG;
-    p.ntiles = idx->NG;
-    p.ragged = uint32_t(idx->r % 64);
-    p.ctl = d_ctl;
-    p.U = reinterpret_cast<uint64_t*>(blk + kOffU);
-    p.aggs = reinterpret_cast<uint32_t*>(blk + kOffAggs);
+    choose_class(n, T, &cls, &zmode);
+    const QDesc qd{0, n, T, zmode};
+    const uint32_t slot0 = 0;
+    if ((e = cudaMemcpyAsync(blk, &qd, sizeof qd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(blk + kOffList, &slot0, sizeof slot0, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(blk + kOffIds, ids, sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return cuda_error(e, "upload query");
     int per_sm = 0;
-    if ((e = k->occupancy(&per_sm)) != cudaSuccess) return cuda_error(e, "occupancy");
-    const uint64_t grid = std::min<uint64_t>((idx->NG + kNW - 1) / kNW,
-                                             uint64_t(std::max(per_sm, 1)) * idx->num_sms);
-    if ((e = k->launch(p, int(std::max<uint64_t>(grid, 1)), st)) != cudaSuccess)
-        return cuda_error(e, "launch threshold kernel");
-    WriteParams w{};
-    w.U = p.U;
-    w.aggs = p.aggs;
-    w.pref = reinterpret_cast<uint32_t*>(blk + kOffPref);
-    w.bagg = reinterpret_cast<uint32_t*>(blk + kOffBagg);
-    w.bpref = reinterpret_cast<uint32_t*>(blk + kOffBpref);
-    w.out = out;
-    w.cap = cap;
-    w.W = idx->W;
-    w.NG = idx->NG;
-    w.ctl = d_ctl;
-    if ((e = launch_reencode(w, st)) != cudaSuccess) return cuda_error(e, "launch re-encoding");
-    uint32_t h[4] = {0, 0, 0, 0};
-    if ((e = cudaMemcpyAsync(h, d_ctl, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    if ((e = class_occupancy(cls, &per_sm)) != cudaSuccess) return cuda_error(e, "occupancy");
+    Launch L{cls, 0, 1, 0, 1};
+    L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>((idx->NG + kNW - 1) / kNW,
+                                                          uint64_t(std::max(per_sm, 1)) *
+                                                              idx->num_sms)));
+    const ChunkPlan ch{0, 1, 0, 1};
+    ExecBufs b{};
+    b.qd = reinterpret_cast<const QDesc*>(blk);
+    b.lists = reinterpret_cast<const uint32_t*>(blk + kOffList);
+    b.ids = reinterpret_cast<const uint32_t*>(blk + kOffIds);
+    b.scratch = blk + kOffScratch;
+    b.lay = lay;
+    b.out = out;
+    b.cap = cap;
+    if ((e = enqueue_plan(idx, &ch, 1, &L, b, st, nullptr, 0, nullptr, 0, nullptr)) !=
+        cudaSuccess)
+        return cuda_error(e, "launch query kernels");
+    unsigned long long h[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(h, b.scratch + lay.res, sizeof h, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
         return cuda_error(e, "read result length");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "query");
-    *out_len = uint64_t(h[2]) | (uint64_t(h[3]) << 32);
+    *out_len = h[1];
     if (*out_len > cap) return report_error(THR_E_NOSPACE, "output buffer too small");
     return THR_OK;
 }

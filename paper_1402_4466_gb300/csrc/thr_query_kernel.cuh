@@ -1,6 +1,7 @@
-// The fused threshold kernel k_threshold<S> (see thr_device.cuh for the
-// index layout and the outline).  S = counter width; the host picks the
-// smallest instantiated S with 2^S > the threshold the counters test.
+// Pass A of a batch of threshold queries (see thr_device.cuh for the index
+// layout and the outline): the counting kernels k_threshold<S> (carry-save,
+// S = counter width; the host picks the smallest instantiated S with 2^S >
+// the threshold the counters test) and, in thr_scancount.cu, k_scancount.
 #pragma once
 
 #include "thr_device.cuh"
@@ -20,14 +21,28 @@ constexpr int kMetaBatch = 32;  // mask records staged per round trip
 
 struct WarpSmem {
     uint4 rec[kCH];
-    uint4 meta[kMetaBatch][4];   // mask records of kMetaBatch consecutive inputs
-    unsigned long long tw[kGW];  // the subtile's result words, for the scan
+    uint4 meta[kMetaBatch][4];     // mask records of kMetaBatch consecutive inputs
+    unsigned long long tw[kGW];    // the subtile's result words, for the scan
+    unsigned long long woff[kCH];  // stream offsets of the current query's ids
+    uint32_t ids[kCH];             //   and the ids, when n <= kCH
+    uint32_t qn, qT, qz, qoff;     // the current query: n, T, zmode, first id
 };
 
 struct CtaSmem {
     WarpSmem w[kNW];
-    uint32_t ids[kCH];             // the query's ids, when n <= kCH
-    unsigned long long woff[kCH];  // their stream offsets
+};
+
+// The query a warp works on, read from its WarpSmem copy at every use (the
+// loads are cheap; keeping the values in registers would spill).  cached:
+// n <= kCH and ids / woff of WarpSmem hold its ids and their stream offsets.
+struct QView {
+    const volatile WarpSmem& w;
+    const uint32_t* all_ids;
+    __device__ __forceinline__ uint32_t n() const { return w.qn; }
+    __device__ __forceinline__ uint32_t T() const { return w.qT; }
+    __device__ __forceinline__ uint32_t zmode() const { return w.qz; }
+    __device__ __forceinline__ const uint32_t* ids() const { return all_ids + w.qoff; }
+    __device__ __forceinline__ bool cached() const { return w.qn <= uint32_t(kCH); }
 };
 
 constexpr size_t cta_smem_bytes() { return sizeof(CtaSmem); }
@@ -43,7 +58,7 @@ constexpr size_t cta_smem_bytes() { return sizeof(CtaSmem); }
 // of the group is issued.
 // Stage the mask records of inputs m0 .. m0 + kMetaBatch - 1 (lane: 16
 // bytes of 4 records); literal runs and absent ones-fill masks are skipped.
-__device__ __forceinline__ void stage_masks(const QueryParams& p, WarpSmem& ws, uint32_t m0,
+__device__ __forceinline__ void stage_masks(const PassAParams& p, WarpSmem& ws, uint32_t m0,
                                            uint32_t nrec, uint32_t lane) {
     const uint32_t part = lane & 3;
 #pragma unroll
@@ -61,7 +76,7 @@ __device__ __forceinline__ void stage_masks(const QueryParams& p, WarpSmem& ws, 
     __syncwarp();
 }
 
-__device__ __forceinline__ void decode_group(const QueryParams& p, WarpSmem& ws,
+__device__ __forceinline__ void decode_group(const PassAParams& p, WarpSmem& ws,
                                              uint32_t r0, uint32_t nrec, uint32_t x0,
                                              uint32_t x1, uint32_t lane,
                                              uint64_t (&v)[kGroup][kRows]) {
@@ -138,9 +153,9 @@ struct CsaCount {
 // r = 0..3, words x0 + 32 r + lane (zero past x1).  Count is the counting
 // policy (carry-save bit slices, or ScanCount counters).
 template <class Count>
-__device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSmem& sm,
-                                               bool cached, uint32_t x0, uint32_t x1,
-                                               uint32_t lane, WarpSmem& ws, Count& count,
+__device__ __forceinline__ void subtile_result(const PassAParams& p, const QView& q,
+                                               uint32_t x0, uint32_t x1, uint32_t lane,
+                                               WarpSmem& ws, Count& count,
                                                uint64_t (&o)[kRows]) {
 #pragma unroll
     for (int q = 0; q < kRows; ++q) o[q] = 0;
@@ -148,21 +163,21 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
     const uint32_t g = x0 / kGW;
     count.begin();
     uint32_t k_ones = 0, d_act = 0;
-    const bool one_chunk = p.n <= uint32_t(kCH);
+    const bool one_chunk = q.n() <= uint32_t(kCH);
     bool pruned = false;
     if (!one_chunk) {  // classify every input first so that pruning still applies
-        for (uint32_t i0 = 0; i0 < p.n; i0 += 32) {
+        for (uint32_t i0 = 0; i0 < q.n(); i0 += 32) {
             const uint32_t i = i0 + lane;
             uint32_t cls = 0;
-            if (i < p.n) cls = uint32_t(__ldg(p.sdesc + uint64_t(__ldg(p.ids + i)) * p.NG + g) & 3u);
+            if (i < q.n()) cls = uint32_t(__ldg(p.sdesc + uint64_t(__ldg(q.ids() + i)) * p.NG + g) & 3u);
             k_ones += __popc(__ballot_sync(~0u, cls == 1));
             d_act += __popc(__ballot_sync(~0u, cls >= 2));
         }
-        const int64_t Tp = int64_t(p.T) - int64_t(k_ones);
+        const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
         pruned = Tp <= 0 || Tp > int64_t(d_act);
     }
-    for (uint32_t c0 = 0; c0 < p.n && !pruned; c0 += kCH) {
-        const uint32_t cn = min(uint32_t(kCH), p.n - c0);
+    for (uint32_t c0 = 0; c0 < q.n() && !pruned; c0 += kCH) {
+        const uint32_t cn = min(uint32_t(kCH), q.n() - c0);
         uint32_t nrec = 0;
         // 1. classify, lane per input, from the subtile descriptor
         for (uint32_t i0 = 0; i0 < cn; i0 += 32) {
@@ -170,11 +185,11 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
             uint32_t cls = 0;  // 0 zero fill, 1 ones fill, 2 literal run, 3 mixed
             uint4 r = make_uint4(0, 0, 0, 0);
             if (i < cn) {
-                const uint32_t b = cached ? sm.ids[i] : __ldg(p.ids + c0 + i);
+                const uint32_t b = q.cached() ? ws.ids[i] : __ldg(q.ids() + c0 + i);
                 const uint64_t sd = __ldg(p.sdesc + uint64_t(b) * p.NG + g);
                 cls = uint32_t(sd & 3u);
                 if (cls >= 2) {
-                    const uint64_t woff = cached ? sm.woff[i] : p.desc[b].woff;
+                    const uint64_t woff = q.cached() ? ws.woff[i] : p.desc[b].woff;
                     const uint64_t field = sd >> 19;
                     if (cls == 2) {
                         const uint64_t ra = woff + field;
@@ -194,7 +209,7 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
         __syncwarp();
         if (one_chunk) {  // run-aware pruning (Sec. 6.4 cases 1 and 2)
             d_act = nrec;
-            const int64_t Tp = int64_t(p.T) - int64_t(k_ones);
+            const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
             if (Tp <= 0 || Tp > int64_t(d_act)) break;
         }
         // 2. the active inputs into the counters, a group at a time
@@ -205,7 +220,7 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
             }
             uint64_t v[kGroup][kRows];
             decode_group(p, ws, r0, nrec, x0, x1, lane, v);
-            if (p.zmode) {  // count the zeros of the active inputs
+            if (q.zmode()) {  // count the zeros of the active inputs
 #pragma unroll
                 for (int j = 0; j < kGroup; ++j)
 #pragma unroll
@@ -217,13 +232,13 @@ __device__ __forceinline__ void subtile_result(const QueryParams& p, const CtaSm
         __syncwarp();
     }
     // 3. compare with T' = T - k (or the zeros with d - T' + 1)
-    const int64_t Tp = int64_t(p.T) - int64_t(k_ones);
+    const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
     if (Tp <= 0) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) o[r] = ~0ull;
     } else if (Tp <= int64_t(d_act)) {
-        const uint32_t thr = p.zmode ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
-        count.finish(thr, p.zmode ? ~0u : 0u, o);
+        const uint32_t thr = q.zmode() ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
+        count.finish(thr, q.zmode() ? ~0u : 0u, o);
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -321,50 +336,75 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
 }
 
 // Pass A driver: each warp of the persistent grid takes every (grid
-// warps)-th 128-word subtile, computes its result words with the counting
-// policy, stores them in the scratch buffer U (skipped when the subtile
-// holds one fill class only) and stores the subtile's re-encoding aggregate.
-// No warp ever waits for another.
+// warps)-th work item of the launch, one (query, subtile) pair: query-major
+// (item i = query list[i / NG], subtile i % NG) or subtile-major (subtile
+// i / nlist of query list[i % nlist], so that queries sharing inputs read
+// them at about the same time).  It computes the subtile's result words with
+// the counting policy, stores them in the query's scratch words U (skipped
+// when the subtile holds one fill class only) and stores the subtile's
+// re-encoding aggregate.  No warp ever waits for another.
 template <class Count>
-__device__ __forceinline__ void pass_a(const QueryParams& p, CtaSmem& sm, Count& count) {
-    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // the query's ids and their stream offsets, once per CTA
-    const bool cached = p.n <= uint32_t(kCH);
-    if (cached) {
-        for (uint32_t i = tid; i < p.n; i += kNT) {
-            const uint32_t b = __ldg(p.ids + i);
-            sm.ids[i] = b;
-            sm.woff[i] = p.desc[b].woff;
-        }
-    }
-    __syncthreads();
+__device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count& count) {
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem& ws = sm.w[wid];
     const uint32_t nwarps = gridDim.x * kNW;
-    for (uint32_t g = blockIdx.x * kNW + wid; g < p.ntiles; g += nwarps) {
+    const uint32_t nitems = p.nlist * p.NG;
+    uint32_t cur = ~0u;  // slot whose ids the warp holds
+    const QView q{ws, p.ids};
+    for (uint32_t it = blockIdx.x * kNW + wid; it < nitems; it += nwarps) {
+        uint32_t li, g;
+        if (p.order) {
+            g = it / p.nlist;
+            li = it - g * p.nlist;
+        } else {
+            li = it / p.NG;
+            g = it - li * p.NG;
+        }
+        const uint32_t s = __ldg(p.list + li);
+        if (s != cur) {  // a new query: its parameters, and its ids when they fit
+            const QDesc d = p.qd[s];
+            __syncwarp();
+            if (lane == 0) {
+                ws.qn = d.n;
+                ws.qT = d.T;
+                ws.qz = d.zmode;
+                ws.qoff = d.ids_off;
+            }
+            if (d.n <= uint32_t(kCH)) {
+                for (uint32_t i = lane; i < d.n; i += 32) {
+                    const uint32_t b = __ldg(p.ids + d.ids_off + i);
+                    ws.ids[i] = b;
+                    ws.woff[i] = p.desc[b].woff;
+                }
+            }
+            __syncwarp();
+            cur = s;
+        }
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint64_t orow[kRows];
-        subtile_result(p, sm, cached, x0, x1, lane, ws, count, orow);
+        subtile_result(p, q, x0, x1, lane, ws, count, orow);
         // rows -> 4 consecutive words per lane (the scan's order)
 #pragma unroll
         for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
         __syncwarp();
         uint64_t o[kWPL];
 #pragma unroll
-        for (int q = 0; q < kWPL; ++q) o[q] = ws.tw[kWPL * lane + q];
+        for (int k = 0; k < kWPL; ++k) o[k] = ws.tw[kWPL * lane + k];
         __syncwarp();
         const LocalScan L = local_scan(x0, x1, lane, o);
+        const uint64_t sg = uint64_t(cur) * p.NG + g;
         if (L.A.nh || L.A.nl) {
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) p.U[uint64_t(x0) + 32 * r + lane] = orow[r];
+            for (int r = 0; r < kRows; ++r) p.U[sg * kGW + 32 * r + lane] = orow[r];
         }
-        if (lane == 0) agg_store_plain(p.aggs + uint64_t(g) * kAggWords, L.A);
+        if (lane == 0) agg_store_plain(p.aggs + sg * kAggWords, L.A);
     }
 }
 
 // Pass A with the carry-save counters (S-bit saturating bit slices).
 template <int S>
-__global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_threshold(const QueryParams p) {
+__global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_threshold(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     CsaCount<S> count;

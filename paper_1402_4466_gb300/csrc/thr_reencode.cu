@@ -1,13 +1,18 @@
-// Passes B and C of the canonical re-encoding of a query result.
+// Passes B and C of the canonical re-encoding of the results of a chunk of
+// queries (slots 0 .. Q-1).
 //
-// Pass A (k_threshold) left, per 128-word subtile g, its result words in U
-// (unless the subtile holds a single fill class) and its aggregate A_g over
+// Pass A left, per slot s and 128-word subtile g, the result words in U
+// (unless the subtile holds a single fill class) and the aggregate A_g over
 // the monoid of thr_device.cuh (heads, literals, last head, boundary
-// classes).  Pass B scans the aggregates in order (one CTA; the word 0 of the
+// classes).  Pass B scans each slot's aggregates in order (word 0 of a
 // bitmap always starts the first group) into the prefix before every
-// subtile and writes the marker of the group that ends at word W and the
-// total length.  Pass C gives every literal and every marker whose group
-// ends inside subtile g its position: heads before + literals before.
+// subtile and the aggregate of the whole result, whose heads + literals are
+// the encoded length; the last CTA of the chunk then scans the lengths over
+// the slots, which places each result in the output pool after those of the
+// earlier slots and chunks, and writes each result's final marker (the group
+// that ends at word W).  Pass C gives every literal and every marker whose
+// group ends inside subtile g its position: result offset + heads before +
+// literals before.
 #include "thr_query_kernel.cuh"
 
 namespace thr {
@@ -71,9 +76,32 @@ __device__ __forceinline__ void warp_scan(RangeAgg& v, bool& have, uint32_t lane
 constexpr uint32_t kScanBlock = 256;
 constexpr uint32_t kEmpty = 1u << 8;
 
-__device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t g) {
-    RangeAgg a = agg_load_plain(w.aggs + uint64_t(g) * kAggWords);
+__device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t s, uint32_t g) {
+    RangeAgg a = agg_load_plain(w.aggs + (uint64_t(s) * w.NG + g) * kAggWords);
     return g == 0 ? fix_first(a) : a;
+}
+
+// Exclusive sum over the CTA (kScanBlock threads) and the total.
+__device__ __forceinline__ unsigned long long block_exsum(unsigned long long v,
+                                                          unsigned long long& total) {
+    __shared__ unsigned long long wsum[kScanBlock / 32];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long t = __shfl_up_sync(~0u, inc, d);
+        if (lane >= uint32_t(d)) inc += t;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned long long before = 0;
+    total = 0;
+    for (uint32_t k = 0; k < kScanBlock / 32; ++k) {
+        if (k < wid) before += wsum[k];
+        total += wsum[k];
+    }
+    __syncthreads();
+    return before + inc - v;
 }
 
 // Exclusive ordered scan over the CTA (kScanBlock threads); returns the
@@ -126,73 +154,108 @@ __device__ __forceinline__ RangeAgg block_scan(RangeAgg v, bool vh, bool& eh, Ra
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_aggs(WriteParams w) {
-    const uint32_t g = blockIdx.x * kScanBlock + threadIdx.x;
+    const uint32_t s = blockIdx.x / w.NB, b = blockIdx.x - s * w.NB;
+    const uint32_t g = b * kScanBlock + threadIdx.x;
     RangeAgg a{};
     const bool ah = g < w.NG;
-    if (ah) a = load_agg(w, g);
+    if (ah) a = load_agg(w, s, g);
     bool eh, th;
     RangeAgg total;
     RangeAgg E = block_scan(a, ah, eh, total, th);
     if (ah) {
         if (!eh) E.cls = kEmpty;
-        agg_store_plain(w.pref + uint64_t(g) * kAggWords, E);
+        agg_store_plain(w.pref + (uint64_t(s) * w.NG + g) * kAggWords, E);
     }
-    __shared__ bool last_block;
+    __shared__ bool last_block, last_slot;
     if (threadIdx.x == 0) {
-        agg_store_plain(w.bagg + uint64_t(blockIdx.x) * kAggWords, total);
+        agg_store_plain(w.bagg + (uint64_t(s) * w.NB + b) * kAggWords, total);
         __threadfence();
-        last_block = atomicAdd(w.ctl + 4, 1u) == gridDim.x - 1;
+        last_block = atomicAdd(w.tick + s, 1u) == w.NB - 1;
     }
     __syncthreads();
     if (!last_block) return;
     __threadfence();
-    // the last CTA: exclusive prefixes of the block totals, kScanBlock at a time
+    // the slot's last CTA: exclusive prefixes of its block totals
     RangeAgg carry{};
     bool ch = false;
-    for (uint32_t b0 = 0; b0 < gridDim.x; b0 += kScanBlock) {
-        const uint32_t b = b0 + threadIdx.x;
+    for (uint32_t b0 = 0; b0 < w.NB; b0 += kScanBlock) {
+        const uint32_t bb = b0 + threadIdx.x;
         RangeAgg x{};
-        const bool xh = b < gridDim.x;
-        if (xh) x = agg_load_plain(w.bagg + uint64_t(b) * kAggWords);
+        const bool xh = bb < w.NB;
+        if (xh) x = agg_load_plain(w.bagg + (uint64_t(s) * w.NB + bb) * kAggWords);
         bool ebh, cth;
         RangeAgg ctot;
         RangeAgg Eb = block_scan(x, xh, ebh, ctot, cth);
-        if (ch) {  // prepend the totals of the earlier chunks
+        if (ch) {  // prepend the totals of the earlier block groups
             Eb = ebh ? agg_combine(carry, Eb) : carry;
             ebh = true;
         }
         if (xh) {
             if (!ebh) Eb.cls = kEmpty;
-            agg_store_plain(w.bpref + uint64_t(b) * kAggWords, Eb);
+            agg_store_plain(w.bpref + (uint64_t(s) * w.NB + bb) * kAggWords, Eb);
         }
         if (cth) {
             carry = ch ? agg_combine(carry, ctot) : ctot;
             ch = true;
         }
     }
-    if (threadIdx.x == 0) {  // carry covers the whole bitmap
-        const RangeAgg& E2 = carry;
-        const uint64_t L = uint64_t(E2.nl) - E2.lp;
-        const uint64_t F = uint64_t(w.W) - E2.lh - L;
-        const uint64_t b = (F && agg_lhc(E2) == 1u) ? 1ull : 0ull;
-        const uint64_t pos = uint64_t(E2.nh) - 1 + E2.lp;
-        if (pos < w.cap) w.out[pos] = b | (F << 1) | (L << 33);
-        *reinterpret_cast<unsigned long long*>(w.ctl + 2) = uint64_t(E2.nh) + uint64_t(E2.nl);
+    if (threadIdx.x == 0) {  // carry covers the whole result of slot s
+        agg_store_plain(w.full + uint64_t(s) * kAggWords, carry);
+        w.tick[s] = 0;
+        __threadfence();
+        last_slot = atomicAdd(w.gtick, 1u) == w.Q - 1;
+    }
+    __syncthreads();
+    if (!last_slot) return;
+    __threadfence();
+    // the chunk's last CTA: place the results of its slots in the pool and
+    // write the marker of each result's last group
+    unsigned long long run = *w.base;
+    for (uint32_t s0 = 0; s0 < w.Q; s0 += kScanBlock) {
+        const uint32_t t = s0 + threadIdx.x;
+        RangeAgg F{};
+        unsigned long long len = 0;
+        if (t < w.Q) {
+            F = agg_load_plain(w.full + uint64_t(t) * kAggWords);
+            len = uint64_t(F.nh) + F.nl;
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_exsum(len, tot);
+        if (t < w.Q) {
+            const unsigned long long off = run + ex;
+            w.res[2 * (uint64_t(w.q0) + t)] = off;
+            w.res[2 * (uint64_t(w.q0) + t) + 1] = len;
+            const uint64_t L = uint64_t(F.nl) - F.lp;
+            const uint64_t Fw = uint64_t(w.W) - F.lh - L;
+            const uint64_t bit = (Fw && agg_lhc(F) == 1u) ? 1ull : 0ull;
+            const uint64_t pos = off + uint64_t(F.nh) - 1 + F.lp;
+            if (pos < w.cap) w.out[pos] = bit | (Fw << 1) | (L << 33);
+        }
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        *w.base = run;
+        *w.gtick = 0;
     }
 }
 
 // One warp per subtile.
 __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t g = blockIdx.x * kNW + (threadIdx.x >> 5);
-    if (g >= w.NG) return;
+    const uint64_t gi = uint64_t(blockIdx.x) * kNW + (threadIdx.x >> 5);
+    const uint32_t s = uint32_t(gi / w.NG);
+    if (s >= w.Q) return;
+    const uint32_t g = uint32_t(gi - uint64_t(s) * w.NG);
+    const uint64_t sg = uint64_t(s) * w.NG + g;
+    const unsigned long long off = w.res[2 * (uint64_t(w.q0) + s)];
     const uint32_t x0 = g * uint32_t(kGW);
     const uint32_t x1 = min(x0 + uint32_t(kGW), w.W);
     const uint32_t xb = x0 + kWPL * lane;
-    const RangeAgg A = agg_load_plain(w.aggs + uint64_t(g) * kAggWords);
+    const RangeAgg A = agg_load_plain(w.aggs + sg * kAggWords);
     uint64_t o[kWPL];
     if (A.nh || A.nl) {
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(w.U + xb);
+        const ulonglong2* src =
+            reinterpret_cast<const ulonglong2*>(w.U + uint64_t(s) * w.NG * kGW + xb);
         const ulonglong2 a = src[0], b = src[1];
         o[0] = a.x;
         o[1] = a.y;
@@ -211,10 +274,11 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
         P.start = P.nh = P.nl = P.lh = P.lp = P.cls = 0;
         hf = 1;
     } else {
-        const RangeAgg inb = agg_load_plain(w.pref + uint64_t(g) * kAggWords);
+        const RangeAgg inb = agg_load_plain(w.pref + sg * kAggWords);
         const uint32_t blk = g / kScanBlock;
         if (blk > 0) {
-            const RangeAgg bp = agg_load_plain(w.bpref + uint64_t(blk) * kAggWords);
+            const RangeAgg bp =
+                agg_load_plain(w.bpref + (uint64_t(s) * w.NB + blk) * kAggWords);
             P = (inb.cls & kEmpty) ? bp : agg_combine(bp, inb);
         } else {
             P = inb;  // g > 0, so subtile 0 is before it in the block
@@ -252,7 +316,7 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
                 const uint64_t Lw = Lc - lg;
                 const uint64_t F = uint64_t(x - hp) - Lw;
                 const uint64_t b = (F && hcls == 1u) ? 1ull : 0ull;
-                const uint64_t pos = uint64_t(J) - 1 + lg;
+                const uint64_t pos = off + uint64_t(J) - 1 + lg;
                 if (pos < w.cap) w.out[pos] = b | (F << 1) | (Lw << 33);
             }
             hp = x;
@@ -262,7 +326,7 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
             ++J;
         }
         if (c == 2u) {
-            const uint64_t pos = uint64_t(J) + Lc;
+            const uint64_t pos = off + uint64_t(J) + Lc;
             if (pos < w.cap) w.out[pos] = o[q];
             ++Lc;
         }
@@ -272,11 +336,11 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
 }  // namespace
 
 cudaError_t launch_reencode(const WriteParams& w, cudaStream_t st) {
-    k_scan_aggs<<<(w.NG + kScanBlock - 1) / kScanBlock, kScanBlock, 0, st>>>(w);
+    k_scan_aggs<<<uint64_t(w.Q) * w.NB, kScanBlock, 0, st>>>(w);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-
-    k_write_out<<<(w.NG + kNW - 1) / kNW, kNT, 0, st>>>(w);
+    const uint64_t warps = uint64_t(w.Q) * w.NG;
+    k_write_out<<<(warps + kNW - 1) / kNW, kNT, 0, st>>>(w);
     return cudaGetLastError();
 }
 

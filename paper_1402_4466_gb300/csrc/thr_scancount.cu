@@ -68,7 +68,7 @@ struct ScanCount {
     }
 };
 
-__global__ void __launch_bounds__(kNT) k_scancount(const QueryParams p) {
+__global__ void __launch_bounds__(kNT) k_scancount(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -90,7 +90,7 @@ cudaError_t prepare() {
 
 }  // namespace
 
-cudaError_t launch_scancount(const QueryParams& p, int grid, cudaStream_t st) {
+cudaError_t launch_scancount(const PassAParams& p, int grid, cudaStream_t st) {
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     k_scancount<<<grid, kNT, scancount_smem(), st>>>(p);

@@ -104,10 +104,9 @@ def test_plain_workload():
         p.check(list(range(synth.PLAIN_N)), T)
 
 
-def test_many_criteria_full_size():
+def test_many_criteria_full_size(many_criteria_full):
     """64 bitmaps over 2^26 rows; the thresholds the benchmark times."""
-    r = synth.MANY_R
-    words, _ = synth.many_criteria(0, synth.MANY_N, r)
+    words, r = many_criteria_full
     p = Pair(words, r)
     ids = list(range(synth.MANY_N))
     for T in synth.MANY_TS:
@@ -227,9 +226,8 @@ def test_scancount_several_tiles_and_duplicates():
     p.check(ids, 30, SC)
 
 
-def test_scancount_many_criteria_full_size():
-    r = synth.MANY_R
-    words, _ = synth.many_criteria(0, synth.MANY_N, r)
+def test_scancount_many_criteria_full_size(many_criteria_full):
+    words, r = many_criteria_full
     p = Pair(words, r)
     for T in (2, 16):
         p.check(list(range(synth.MANY_N)), T, SC)
