@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-query", type=int, default=None, metavar="T",
+                    help="build the workload, run one warm-up query at threshold T and "
+                         "then one more (the launch to capture with a profiler); no timing")
+    ap.add_argument("--variant", default="csa", choices=["csa", "position", "scancount"],
+                    help="counting variant of --profile-query")
     return ap.parse_args()
 
 
@@ -208,6 +213,8 @@ def run_ours(args):
     except Exception:
         uuid = None
     clocks = ClockSampler(uuid)  # from the warm-up on, so that it has samples under load
+    # launch configuration of single queries of this shape (autotuner)
+    single_cfg, single_tune_ms = thr.thr_autotune(idx, [(ids, Ts[0])], reps=3, stream=stream)
     for _ in range(args.warmup):
         for T in Ts:
             one_query(T, False)
@@ -233,6 +240,23 @@ def run_ours(args):
     nq = len(q_ms) * world
     value = nq / (total_ms / 1e3)
     input_gbs = (in_bytes * nq) / (total_ms / 1e3) / 1e9
+
+    # pass-A time of each counting variant on the step's queries (events,
+    # L2 flushed before each query)
+    variant_ms = {}
+    for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("position", thr.THR_VARIANT_POSITION),
+                         ("scancount", thr.THR_VARIANT_SCANCOUNT)):
+        per_t = {}
+        for T in Ts:
+            ts = []
+            for _ in range(max(args.steps, 3)):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                stream.synchronize()
+                thr.thr_query(idx, ids, T, out=dout, flags=vflag | thr.THR_PROFILE, stream=stream)
+                ts.append(thr.thr_last_kernel_ms())
+            per_t[str(T)] = round(statistics.median(ts), 5)
+        variant_ms[vname] = per_t
 
     # batched: the step's queries as one thr_query_batch call, replayed as a
     # CUDA graph, with the launch configuration the autotuner picks; timed on
@@ -325,8 +349,10 @@ def run_ours(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(), "peak_kind": peak_kind,
                      "kernel": "k_threshold", "bytes_per_launch": int(avg_bytes),
-                     "kernel_ms": round(avg_kms, 5)},
+                     "kernel_ms": round(avg_kms, 5), "launch_config": single_cfg,
+                     "autotune_ms": [round(t, 4) for t in single_tune_ms]},
         "batched": batched,
+        "pass_a_ms_by_variant": variant_ms,
         "gpu_launches": 3 * len(q_ms),  # passes A, B and C per query
         "clocks": clk,
     }
@@ -402,9 +428,32 @@ def run_reference(args):
     }), flush=True)
 
 
+def profile_query(args):
+    """One warm-up query and one captured query of the many-criteria workload
+    (for ncu: the second launch of each kernel is the one to capture)."""
+    import torch
+
+    import paper_1402_4466_gb300 as thr
+    torch.cuda.init()
+    r, gw, goff = make_index_inputs(args.seed)
+    idx = thr.idx_build_rle(gw, goff, r)
+    flag = {"csa": thr.THR_VARIANT_CSA, "position": thr.THR_VARIANT_POSITION,
+            "scancount": thr.THR_VARIANT_SCANCOUNT}[args.variant]
+    ids = np.arange(synth.MANY_N, dtype=np.uint32)
+    dout = torch.empty(idx.nwords + 1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        n = thr.thr_query(idx, ids, args.profile_query, out=dout, flags=flag)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_query": args.profile_query, "variant": args.variant,
+                      "output_words": n, "input_bytes": 8 * int(goff[-1])}))
+    idx.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_query is not None:
+        profile_query(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

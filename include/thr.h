@@ -71,12 +71,21 @@ typedef enum {
 /* Counting kernel of a query (thr_query; thr_query_batch with
  * THR_POLICY_PLAIN uses it for every query):
  *   THR_VARIANT_CSA        carry-save bit-sliced counters in registers
- *                          (default; any n and T)
+ *                          (default; any n and T), inputs decoded four at a
+ *                          time; when T is close to n the zeros of the
+ *                          active inputs are counted instead, which needs
+ *                          fewer counter bits
+ *   THR_VARIANT_POSITION   the same counters counting ones; inputs that mix
+ *                          fills and literals inside a 128-word subtile are
+ *                          decoded position by position (each lane walks the
+ *                          inputs with a literal at its word), so their cost
+ *                          follows their literals: for sparse inputs
  *   THR_VARIANT_SCANCOUNT  ScanCount: one byte counter per row in shared
  *                          memory per subtile (Sec. 5.1), for very sparse
  *                          inputs; used when n <= 255, else CSA runs */
 #define THR_VARIANT_CSA 0x000u
 #define THR_VARIANT_SCANCOUNT 0x200u
+#define THR_VARIANT_POSITION 0x400u
 #define THR_VARIANT_MASK 0xE00u
 
 /*
@@ -168,6 +177,36 @@ thr_status thr_query_static(const thr_index *idx, const uint32_t *ids, uint32_t 
                             uint32_t T, uint64_t *out, uint64_t cap,
                             uint64_t *out_len, void *cuda_stream);
 
+/*
+ * Serving loop with continuous batching over a resident index.  Requests
+ * (thr_server_submit copies ids) wait in one queue; each of `workers` host
+ * threads owns a CUDA stream and, when free, takes the oldest waiting
+ * requests as one micro-batch: at most max_batch of them, and only as many
+ * as fit mem_budget bytes together with the batches already in flight (a
+ * request claims the scratch of one query slot plus 8 (ceil(r/64) + 1)
+ * bytes for its result; a batch with nothing else in flight always admits
+ * its first request).  The micro-batch runs as thr_query_batch would (CUDA
+ * graph replay; flags: one THR_POLICY_* and THR_VARIANT_* value), so batches
+ * of different workers overlap on the device.  thr_server_wait blocks until
+ * the request is done, copies its result (THR_E_NOSPACE if cap is too
+ * small, *out_len = its length), gives the time from submit to completion
+ * and releases the ticket.  Results equal thr_query's for the same query.
+ * thr_server_stats fills 8 counters: queries done, micro-batches run,
+ * queries in them, most batches in flight at once, largest batch, most
+ * budget bytes claimed at once, requests waiting, batches in flight now.
+ * thr_server_free finishes every waiting request, then stops the workers;
+ * the index must outlive the server.
+ */
+typedef struct thr_server thr_server;
+thr_status thr_server_create(const thr_index *idx, uint32_t workers, uint32_t max_batch,
+                             uint64_t mem_budget, uint32_t flags, thr_server **out);
+thr_status thr_server_submit(thr_server *srv, const uint32_t *ids, uint32_t n, uint32_t T,
+                             uint64_t *ticket);
+thr_status thr_server_wait(thr_server *srv, uint64_t ticket, uint64_t *out, uint64_t cap,
+                           uint64_t *out_len, double *latency_ms);
+thr_status thr_server_stats(thr_server *srv, uint64_t *stats);
+void thr_server_free(thr_server *srv);
+
 /* Release an index (NULL-safe); waits for in-flight work on its device. */
 void idx_free(thr_index *idx);
 
@@ -185,6 +224,11 @@ thr_status idx_info(const thr_index *idx, uint32_t *nbitmaps, uint64_t *r,
 thr_status thr_rle_encode(const uint64_t *words, uint64_t nwords, uint64_t r,
                           uint64_t *out, uint64_t cap, uint64_t *out_len);
 thr_status thr_rle_validate(const uint64_t *stream, uint64_t len, uint64_t r);
+/* The canonical stream of the r-row bitmap whose set rows are
+ * rows[0..nrows) (ascending, repeats allowed, each < r), written like
+ * thr_rle_encode but without forming the uncompressed words.  Host-only. */
+thr_status thr_rle_encode_rows(const uint64_t *rows, uint64_t nrows, uint64_t r,
+                               uint64_t *out, uint64_t cap, uint64_t *out_len);
 
 /*
  * Device time in milliseconds of the query kernel of the last thr_query
@@ -196,21 +240,91 @@ double thr_last_kernel_ms(void);
 /*
  * Autotuner of the batched launch.  Runs the sample batch (arguments as for
  * thr_query_batch; flags: a THR_POLICY_* value and THR_VARIANT_* only) under
- * each of the 8 launch configurations of pass A, reps times each after one
+ * each of the 16 launch configurations of pass A, reps times each after one
  * warm-up run, with L2 flushed before every run, and keeps the fastest for
  * the batch's shape (several kernel classes or one; mean inputs per query)
- * in the index: later thr_query_batch calls of that shape use it.  A
- * configuration is 3 bits: 1 subtile-major work order (queries that share
- * inputs read them at about the same time; else query-major), 2 merge the
- * counter widths of a chunk into one launch, 4 split the SMs among launches
- * that run side by side in proportion to their work.
- *   times  optional, 8 entries: median host time in ms of each configuration
+ * in the index: later thr_query and thr_query_batch calls of that shape use
+ * it.  A configuration is 4 bits: 1 subtile-major work order (queries that
+ * share inputs read them at about the same time; else query-major), 2 merge
+ * the counter widths of a chunk into one launch, 4 split the SMs among
+ * launches that run side by side in proportion to their work, 8 warps take
+ * work items from a counter as they finish (else static striding).
+ *   times  optional, 16 entries: median host time in ms of each configuration
  *   best   optional: the configuration kept
  * Results are identical under every configuration; only the time differs.
  */
 thr_status thr_autotune(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
                         const uint32_t *ids, const uint32_t *T, uint32_t flags,
                         uint32_t reps, void *cuda_stream, double *times, uint32_t *best);
+
+/*
+ * Learned cost model of the variant selector (THR_POLICY_LEARNED).  The
+ * paper predicts each algorithm's time with a fitted model and runs the one
+ * predicted fastest (Sec. 8.1-8.2); here a multilayer perceptron
+ * 16 -> 64 -> 64 -> 3 with ReLU predicts log(pass-A time) of the three
+ * counting variants (0 THR_VARIANT_CSA, 1 THR_VARIANT_POSITION,
+ * 2 THR_VARIANT_SCANCOUNT) from the 16 features of thr_query_features,
+ * normalised as (x - mean) * istd.  Weights are BF16 (FP32 with
+ * THR_SEL_FP32) and every sum is accumulated in FP32; training is minibatch
+ * Adam on the mean squared error over the (row, variant) pairs whose mask
+ * byte is non-zero.  The forward, backward and update steps are CUDA kernels
+ * of this library, on the device current at creation.
+ * Parameters (THR_SEL_PARAMS floats): W1[16][64] b1[64] W2[64][64] b2[64]
+ * W3[64][3] b3[3], y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3.
+ * X: rows x 16 floats, T (targets) and Y: rows x 3 floats, M: rows x 3
+ * bytes; all host arrays.
+ */
+typedef struct thr_selector thr_selector;
+#define THR_SEL_FEATURES 16
+#define THR_SEL_VARIANTS 3
+#define THR_SEL_PARAMS 5443
+#define THR_SEL_FP32 0x1u
+thr_status thr_selector_create(uint64_t seed, uint32_t flags, thr_selector **out);
+void thr_selector_free(thr_selector *sel);
+thr_status thr_selector_set_params(thr_selector *sel, const float *params);
+thr_status thr_selector_get_params(const thr_selector *sel, float *params);
+thr_status thr_selector_set_norm(thr_selector *sel, const float *mean, const float *istd);
+thr_status thr_selector_train(thr_selector *sel, const float *X, const float *T,
+                              const uint8_t *M, uint32_t rows, uint32_t epochs,
+                              uint32_t batch, float lr, uint64_t seed, float *loss);
+thr_status thr_selector_predict(const thr_selector *sel, const float *X, uint32_t rows,
+                                float *Y);
+/* Gradient of the loss over all rows (no update) and the loss itself. */
+thr_status thr_selector_gradients(thr_selector *sel, const float *X, const float *T,
+                                  const uint8_t *M, uint32_t rows, float *grad,
+                                  float *loss);
+/* Features of a query: log2 n, log2 (T + 1), log2 (n - T + 2) (0 if T > n),
+ * log2 r, the quantiles 0, 1/4, 1/2, 3/4, 1 of log2 (compressed words + 1)
+ * over the inputs and log2 of their total, the same quantiles of
+ * log10 (density + 1e-7) and the sum of the densities. */
+thr_status thr_query_features(const thr_index *idx, const uint32_t *ids, uint32_t n,
+                              uint32_t T, float *features);
+/* Attach a cost model to an index (NULL detaches); THR_POLICY_LEARNED then
+ * uses it.  The selector must outlive its use by the index. */
+thr_status thr_index_set_selector(thr_index *idx, const thr_selector *sel);
+
+/*
+ * The counting variant (0 THR_VARIANT_CSA, 1 THR_VARIANT_POSITION,
+ * 2 THR_VARIANT_SCANCOUNT) each query of a batch runs with under the policy
+ * in flags (arguments as for thr_query_batch); nothing is run.
+ */
+thr_status thr_select_variants(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
+                               const uint32_t *ids, const uint32_t *T, uint32_t flags,
+                               uint8_t *variant);
+
+/*
+ * Coefficients of the rule chooser (THR_POLICY_RULE, and THR_POLICY_LEARNED
+ * without a cost model): linear time models in the manner of Sec. 8.1, one
+ * per counting variant, the smallest prediction wins (Sec. 8.2):
+ *   THR_VARIANT_CSA        c[0] + c[1] * words + c[2] * words * S
+ *   THR_VARIANT_POSITION   c[3] + c[4] * words + c[5] * words * S1
+ *   THR_VARIANT_SCANCOUNT  c[6] + c[7] * words + c[8] * set bits
+ * (words: compressed words of the inputs; S: counter bits of the grouped
+ * kernel, S1: counter bits counting ones; set bits: of the inputs), refit
+ * by least squares on measured times.  set (9 values) is applied when
+ * non-NULL, then the current values go to get when non-NULL.
+ */
+thr_status thr_rule_model(const double *set, double *get);
 
 /*
  * Shape of the last thr_query_batch call on this thread: chunks (groups of

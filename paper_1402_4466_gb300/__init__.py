@@ -26,7 +26,7 @@ THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
 THR_NO_GRAPH = 0x1000
-THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT = 0x000, 0x200
+THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",
@@ -34,7 +34,12 @@ STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
 
 # every symbol include/thr.h declares
 ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_free",
-               "thr_last_batch_info", "thr_autotune",
+               "thr_last_batch_info", "thr_autotune", "thr_select_variants", "thr_rule_model",
+               "thr_selector_create", "thr_selector_free", "thr_selector_set_params",
+               "thr_selector_get_params", "thr_selector_set_norm", "thr_selector_train",
+               "thr_selector_predict", "thr_selector_gradients", "thr_query_features",
+               "thr_index_set_selector", "thr_server_create", "thr_server_submit",
+               "thr_server_wait", "thr_server_stats", "thr_server_free", "thr_rle_encode_rows",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -71,6 +76,7 @@ def load():
             lib.idx_info.argtypes = [vp, u32p, u64p, u64p]
             lib.thr_rle_encode.argtypes = [vp, u64, u64, vp, u64, u64p]
             lib.thr_rle_validate.argtypes = [vp, u64, u64]
+            lib.thr_rle_encode_rows.argtypes = [vp, u64, u64, vp, u64, u64p]
             lib.thr_last_error.argtypes = []
             lib.thr_last_error.restype = ctypes.c_char_p
             lib.thr_last_kernel_ms.argtypes = []
@@ -78,9 +84,35 @@ def load():
             i32p = ctypes.POINTER(ctypes.c_int32)
             lib.thr_last_batch_info.argtypes = [u32p, u32p, i32p, u32p]
             lib.thr_autotune.argtypes = [vp, u32, vp, vp, vp, u32, u32, vp, vp, u32p]
+            lib.thr_select_variants.argtypes = [vp, u32, vp, vp, vp, u32, vp]
+            lib.thr_rule_model.argtypes = [vp, vp]
+            lib.thr_selector_create.argtypes = [u64, u32, ctypes.POINTER(vp)]
+            lib.thr_selector_free.argtypes = [vp]
+            lib.thr_selector_free.restype = None
+            lib.thr_selector_set_params.argtypes = [vp, vp]
+            lib.thr_selector_get_params.argtypes = [vp, vp]
+            lib.thr_selector_set_norm.argtypes = [vp, vp, vp]
+            lib.thr_selector_train.argtypes = [vp, vp, vp, vp, u32, u32, u32, ctypes.c_float,
+                                               u64, vp]
+            lib.thr_selector_predict.argtypes = [vp, vp, u32, vp]
+            lib.thr_selector_gradients.argtypes = [vp, vp, vp, vp, u32, vp, vp]
+            lib.thr_query_features.argtypes = [vp, vp, u32, u32, vp]
+            lib.thr_index_set_selector.argtypes = [vp, vp]
+            lib.thr_server_create.argtypes = [vp, u32, u32, u64, u32, ctypes.POINTER(vp)]
+            lib.thr_server_submit.argtypes = [vp, vp, u32, u32, u64p]
+            lib.thr_server_wait.argtypes = [vp, u64, vp, u64, u64p,
+                                            ctypes.POINTER(ctypes.c_double)]
+            lib.thr_server_stats.argtypes = [vp, vp]
+            lib.thr_server_free.argtypes = [vp]
+            lib.thr_server_free.restype = None
             for f in ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_info",
                       "thr_rle_encode", "thr_rle_validate", "thr_last_batch_info",
-                      "thr_autotune"):
+                      "thr_autotune", "thr_select_variants", "thr_rule_model",
+                      "thr_selector_create", "thr_selector_set_params", "thr_selector_get_params",
+                      "thr_selector_set_norm", "thr_selector_train", "thr_selector_predict",
+                      "thr_selector_gradients", "thr_query_features", "thr_index_set_selector",
+                      "thr_server_create", "thr_server_submit", "thr_server_wait",
+                      "thr_server_stats", "thr_rle_encode_rows"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -263,11 +295,11 @@ def _pack(queries):
 
 
 def thr_autotune(idx: Index, queries, flags: int = 0, reps: int = 3, stream=None):
-    """Time the 8 pass-A launch configurations on a sample batch of (ids, T)
+    """Time the 16 pass-A launch configurations on a sample batch of (ids, T)
     queries and keep the fastest for its shape in the index.  Returns
     (best configuration, list of median times in ms)."""
     nq, id_off, ids, T = _pack(queries)
-    times = np.zeros(8, dtype=np.float64)
+    times = np.zeros(16, dtype=np.float64)
     best = ctypes.c_uint32(0)
     _check(load().thr_autotune(ctypes.c_void_p(idx.handle), nq,
                                ctypes.c_void_p(id_off.ctypes.data),
@@ -292,6 +324,18 @@ def thr_rle_encode(words, r: int) -> np.ndarray:
     return out[: n.value].copy()
 
 
+def thr_rle_encode_rows(rows, r: int) -> np.ndarray:
+    """Canonical stream of the bitmap with the given set rows (ascending)."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint64)
+    cap = min(2 * rows.size + 2, (int(r) + 63) // 64 + 1)
+    out = np.empty(max(cap, 1), dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(load().thr_rle_encode_rows(ctypes.c_void_p(rows.ctypes.data if rows.size else 0),
+                                      rows.size, int(r), ctypes.c_void_p(out.ctypes.data),
+                                      out.size, ctypes.byref(n)), "thr_rle_encode_rows")
+    return out[: n.value].copy()
+
+
 def thr_rle_validate(stream, r: int) -> int:
     s = _u64(stream)
     return int(load().thr_rle_validate(ctypes.c_void_p(s.ctypes.data if s.size else 0),
@@ -305,3 +349,188 @@ def encode_many(word_arrays, r: int):
     offs = np.zeros(len(streams) + 1, dtype=np.uint64)
     offs[1:] = np.cumsum([len(s) for s in streams])
     return (np.concatenate(streams) if streams else np.zeros(0, np.uint64)), offs
+
+
+# ------------------------------------------------------------------ selector
+
+SEL_FEATURES, SEL_VARIANTS, SEL_PARAMS = 16, 3, 5443
+THR_SEL_FP32 = 0x1
+VARIANT_FLAGS = (THR_VARIANT_CSA, THR_VARIANT_POSITION, THR_VARIANT_SCANCOUNT)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Selector:
+    """The learned cost model (thr_selector_*): 16 features -> 64 -> 64 -> 3
+    predicted log pass-A times; BF16 weights (FP32 with fp32=True)."""
+
+    def __init__(self, seed: int = 0, fp32: bool = False):
+        h = ctypes.c_void_p(0)
+        _check(load().thr_selector_create(int(seed), THR_SEL_FP32 if fp32 else 0,
+                                          ctypes.byref(h)), "thr_selector_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load().thr_selector_free(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(SEL_PARAMS, np.float32)
+        _check(load().thr_selector_get_params(ctypes.c_void_p(self.handle),
+                                              ctypes.c_void_p(out.ctypes.data)),
+               "thr_selector_get_params")
+        return out
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == SEL_PARAMS
+        _check(load().thr_selector_set_params(ctypes.c_void_p(self.handle),
+                                              ctypes.c_void_p(p.ctypes.data)),
+               "thr_selector_set_params")
+
+    def set_norm(self, mean, istd):
+        mean, istd = _f32(mean), _f32(istd)
+        _check(load().thr_selector_set_norm(ctypes.c_void_p(self.handle),
+                                            ctypes.c_void_p(mean.ctypes.data),
+                                            ctypes.c_void_p(istd.ctypes.data)),
+               "thr_selector_set_norm")
+
+    def train(self, X, T, M, epochs: int, batch: int = 512, lr: float = 1e-3,
+              seed: int = 0) -> float:
+        X, T = _f32(X), _f32(T)
+        M = np.ascontiguousarray(M, dtype=np.uint8)
+        loss = ctypes.c_float(0)
+        _check(load().thr_selector_train(ctypes.c_void_p(self.handle),
+                                         ctypes.c_void_p(X.ctypes.data),
+                                         ctypes.c_void_p(T.ctypes.data),
+                                         ctypes.c_void_p(M.ctypes.data), X.shape[0],
+                                         int(epochs), int(batch), float(lr), int(seed),
+                                         ctypes.byref(loss)), "thr_selector_train")
+        return loss.value
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        Y = np.empty((X.shape[0], SEL_VARIANTS), np.float32)
+        _check(load().thr_selector_predict(ctypes.c_void_p(self.handle),
+                                           ctypes.c_void_p(X.ctypes.data), X.shape[0],
+                                           ctypes.c_void_p(Y.ctypes.data)),
+               "thr_selector_predict")
+        return Y
+
+    def gradients(self, X, T, M):
+        X, T = _f32(X), _f32(T)
+        M = np.ascontiguousarray(M, dtype=np.uint8)
+        g = np.empty(SEL_PARAMS, np.float32)
+        loss = ctypes.c_float(0)
+        _check(load().thr_selector_gradients(ctypes.c_void_p(self.handle),
+                                             ctypes.c_void_p(X.ctypes.data),
+                                             ctypes.c_void_p(T.ctypes.data),
+                                             ctypes.c_void_p(M.ctypes.data), X.shape[0],
+                                             ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)),
+               "thr_selector_gradients")
+        return loss.value, g
+
+
+def query_features(idx: Index, ids, T: int) -> np.ndarray:
+    ids = _u32(ids)
+    f = np.empty(SEL_FEATURES, np.float32)
+    _check(load().thr_query_features(ctypes.c_void_p(idx.handle),
+                                     ctypes.c_void_p(ids.ctypes.data), ids.size, int(T),
+                                     ctypes.c_void_p(f.ctypes.data)), "thr_query_features")
+    return f
+
+
+def set_selector(idx: Index, sel: "Selector | None"):
+    """Attach a cost model to the index (THR_POLICY_LEARNED uses it)."""
+    _check(load().thr_index_set_selector(ctypes.c_void_p(idx.handle),
+                                         ctypes.c_void_p(sel.handle if sel else 0)),
+           "thr_index_set_selector")
+    idx._selector = sel  # keep it alive while attached
+
+
+def select_variants(idx: Index, queries, flags: int) -> np.ndarray:
+    nq, id_off, ids, T = _pack(queries)
+    out = np.zeros(max(nq, 1), np.uint8)
+    _check(load().thr_select_variants(ctypes.c_void_p(idx.handle), nq,
+                                      ctypes.c_void_p(id_off.ctypes.data),
+                                      ctypes.c_void_p(ids.ctypes.data if ids.size else 0),
+                                      ctypes.c_void_p(T.ctypes.data), int(flags),
+                                      ctypes.c_void_p(out.ctypes.data)), "thr_select_variants")
+    return out[:nq]
+
+
+def rule_model(coeffs=None) -> np.ndarray:
+    """Get (and with coeffs, first set) the rule chooser's 9 coefficients."""
+    get = np.zeros(9, np.float64)
+    setp = None
+    if coeffs is not None:
+        setp = np.ascontiguousarray(coeffs, dtype=np.float64)
+        assert setp.size == 9
+    _check(load().thr_rule_model(ctypes.c_void_p(setp.ctypes.data if setp is not None else 0),
+                                 ctypes.c_void_p(get.ctypes.data)), "thr_rule_model")
+    return get
+
+
+# ------------------------------------------------------------------ serving
+
+SERVER_STATS = ("done", "batches", "batched_queries", "max_in_flight", "max_batch",
+                "max_claimed_bytes", "waiting", "in_flight")
+
+
+class Server:
+    """thr_server_*: continuous batching over a resident index.  submit()
+    returns a ticket at once; wait(ticket) blocks for the result stream and
+    its latency (ms, submit to completion)."""
+
+    def __init__(self, idx: Index, workers: int = 4, max_batch: int = 64,
+                 mem_budget: int = 4 << 30, flags: int = 0):
+        h = ctypes.c_void_p(0)
+        _check(load().thr_server_create(ctypes.c_void_p(idx.handle), int(workers),
+                                        int(max_batch), int(mem_budget), int(flags),
+                                        ctypes.byref(h)), "thr_server_create")
+        self.handle = h.value
+        self.idx = idx
+        self._buf = np.empty(idx.nwords + 1, np.uint64)
+
+    def submit(self, ids, T: int) -> int:
+        ids = _u32(ids)
+        t = ctypes.c_uint64(0)
+        _check(load().thr_server_submit(ctypes.c_void_p(self.handle),
+                                        ctypes.c_void_p(ids.ctypes.data), ids.size, int(T),
+                                        ctypes.byref(t)), "thr_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, buf: np.ndarray | None = None):
+        buf = self._buf if buf is None else buf
+        n = ctypes.c_uint64(0)
+        lat = ctypes.c_double(0)
+        _check(load().thr_server_wait(ctypes.c_void_p(self.handle), int(ticket),
+                                      ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                      ctypes.byref(n), ctypes.byref(lat)), "thr_server_wait")
+        return buf[: n.value].copy(), lat.value
+
+    def stats(self) -> dict:
+        a = np.zeros(8, np.uint64)
+        _check(load().thr_server_stats(ctypes.c_void_p(self.handle),
+                                       ctypes.c_void_p(a.ctypes.data)), "thr_server_stats")
+        return {k: int(v) for k, v in zip(SERVER_STATS, a)}
+
+    def close(self):
+        if self.handle:
+            load().thr_server_free(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -67,7 +67,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
             objs = list(ex.map(lambda s: _compile(s, extra), srcs))
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
+               "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

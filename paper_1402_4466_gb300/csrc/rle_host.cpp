@@ -87,6 +87,78 @@ int scan_stream(const uint64_t* s, uint64_t len, uint64_t r, StreamScan* scan,
     return 0;
 }
 
+namespace {
+
+// Canonical group builder: fill words and literal words are fed in order;
+// a group [marker, literals] is emitted when a fill word follows literals,
+// when the fill value changes, or when a counter would overflow.
+struct GroupEncoder {
+    Emitter e;
+    bool open = false;
+    uint64_t gb = 0, gF = 0;
+    std::vector<uint64_t> lits;
+    void flush() {
+        if (!open) return;
+        e.put(marker_word(gF ? gb : 0, gF, lits.size()));
+        for (uint64_t v : lits) e.put(v);
+        lits.clear();
+        open = false;
+    }
+    void fill(uint64_t fb, uint64_t count) {
+        while (count) {
+            if (open && lits.empty() && gb == fb && gF < kFillMax) {
+                const uint64_t take = std::min(count, kFillMax - gF);
+                gF += take;
+                count -= take;
+                continue;
+            }
+            flush();
+            open = true;
+            gb = fb;
+            gF = 0;
+        }
+    }
+    void literal(uint64_t v) {
+        if (open && lits.size() == kLitMax) flush();
+        if (!open) {
+            open = true;
+            gb = 0;
+            gF = 0;
+        }
+        lits.push_back(v);
+    }
+    void word(uint64_t v) {
+        if (is_fill_word(v))
+            fill(v ? 1 : 0, 1);
+        else
+            literal(v);
+    }
+};
+
+}  // namespace
+
+int encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r, uint64_t* out, uint64_t cap,
+                uint64_t* out_len) {
+    const uint64_t W = (r + 63) / 64;
+    if (W > kMaxWords || r == 0) return 1;
+    for (uint64_t i = 0; i < nrows; ++i)
+        if (rows[i] >= r || (i && rows[i] < rows[i - 1])) return 1;
+    GroupEncoder g{Emitter{out, cap}};
+    uint64_t next = 0;  // first word not yet fed
+    for (uint64_t i = 0; i < nrows;) {
+        const uint64_t w = rows[i] / 64;
+        uint64_t v = 0;
+        for (; i < nrows && rows[i] / 64 == w; ++i) v |= 1ull << (rows[i] % 64);
+        if (w > next) g.fill(0, w - next);
+        g.word(v);
+        next = w + 1;
+    }
+    if (W > next) g.fill(0, W - next);
+    g.flush();
+    *out_len = g.e.n;
+    return g.e.n <= cap ? 0 : 4;
+}
+
 int encode_words(const uint64_t* words, uint64_t nwords, uint64_t r,
                  uint64_t* out, uint64_t cap, uint64_t* out_len) {
     const uint64_t W = (r + 63) / 64;

@@ -39,4 +39,11 @@ int scan_stream(const uint64_t* s, uint64_t len, uint64_t r, StreamScan* scan,
 int encode_words(const uint64_t* words, uint64_t nwords, uint64_t r,
                  uint64_t* out, uint64_t cap, uint64_t* out_len);
 
+// Canonical encoding of the bitmap whose set rows are rows[0..nrows)
+// (ascending, repeats allowed, each < r), without forming the uncompressed
+// words.  Returns 0, 1 (bad argument) or 4 (out too small; *out_len still
+// receives the full length).
+int encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r, uint64_t* out, uint64_t cap,
+                uint64_t* out_len);
+
 }  // namespace thr

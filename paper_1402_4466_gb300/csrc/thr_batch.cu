@@ -158,12 +158,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         const uint32_t n = in.id_off[q + 1] - in.id_off[q];
         int cls = 0;
         uint32_t z = 0;
-        choose_class(n, in.T[q], &cls, &z);
-        const int want = in.cls ? in.cls[q] : -1;
-        if (want == kClassScanCount && n <= 255) {
-            cls = kClassScanCount;
-            z = 0;
-        }
+        resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls, &z);
         qd[q] = QDesc{in.id_off[q], n, in.T[q], z};
         qcls[q] = uint8_t(cls);
     }
@@ -182,27 +177,30 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         // the chunk's shape and its launch configuration
         uint32_t present = 0;
         double sum_n = 0;
-        int widest = -1;
+        int widest[3] = {-1, -1, -1};  // per family
         for (uint32_t s = 0; s < Q; ++s) {
             const int c = qcls[q0 + s];
             present |= 1u << c;
             sum_n += qd[q0 + s].n;
-            if (c != kClassScanCount) widest = std::max(widest, c);
+            widest[class_family(c)] = std::max(widest[class_family(c)], c);
         }
         const bool multi = __builtin_popcount(present) > 1;
         uint32_t cfg = opt.force_tune >= 0 ? uint32_t(opt.force_tune)
                                            : tune_lookup(idx, tune_key(multi, sum_n / Q));
         if (opt.force_tune < 0 && env_cfg < kTuneCandidates) cfg = uint32_t(env_cfg);
         if (q0 == 0) first_cfg = cfg;
-        if ((cfg & kTuneMerge) && widest >= 0) {
-            for (uint32_t s = 0; s < Q; ++s)
-                if (qcls[q0 + s] != kClassScanCount) qcls[q0 + s] = uint8_t(widest);
+        if (cfg & kTuneMerge) {  // one counter width per carry-save family
+            for (uint32_t s = 0; s < Q; ++s) {
+                const int fam = class_family(qcls[q0 + s]);
+                if (fam != 1) qcls[q0 + s] = uint8_t(widest[fam]);
+            }
         }
         double work[kNumClasses] = {};
         double work_all = 0;
         for (uint32_t s = 0; s < Q; ++s) {  // cost ~ inputs x counter slices
             const int c = qcls[q0 + s];
-            const double w = double(qd[q0 + s].n) * (c == kClassScanCount ? 4.0 : 2.0 + c);
+            const double w =
+                double(qd[q0 + s].n) * (c == kClassScanCount ? 4.0 : 2.0 + class_width(c));
             work[c] += w;
             work_all += w;
         }
@@ -216,7 +214,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                 CKB(class_occupancy(c, &per_sm[c]), "occupancy");
                 per_sm[c] = std::max(per_sm[c], 1);
             }
-            Launch L{c, off, cnt, (cfg & kTuneOrder) ? 1u : 0u, 1};
+            Launch L{c, off, cnt, (cfg & kTuneOrder) ? 1u : 0u, 1,
+                     (cfg & kTuneDynamic) ? 1u : 0u};
             const uint64_t items = uint64_t(cnt) * NG;
             double ctas = double(per_sm[c]) * idx->num_sms;
             if ((cfg & kTuneSplit) && work_all > 0) ctas *= work[c] / work_all;
@@ -242,7 +241,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     const size_t o_ids = r256(sizeof(QDesc) * nq);
     const size_t o_lists = o_ids + r256(sizeof(uint32_t) * nids);
     const size_t plan_bytes = o_lists + r256(sizeof(uint32_t) * lists.size());
-    const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG);
+    const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG, launches.size());
     const size_t res_bytes = 16 * size_t(nq) + 16;
     unsigned char* pin = nullptr;
     CKB(g_ctx.pinned(plan_bytes + r256(res_bytes), &pin), "pinned staging");

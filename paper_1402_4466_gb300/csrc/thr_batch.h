@@ -19,8 +19,7 @@ struct BatchInput {
     const uint32_t* id_off;  // nq + 1
     const uint32_t* ids;
     const uint32_t* T;
-    const uint8_t* cls;      // requested kernel class per query (kClassScanCount
-                             // or anything else for carry-save), or null
+    const uint8_t* variant;  // counting variant per query (kVar*), or null (kVarCsa)
 };
 
 struct BatchOptions {
@@ -45,8 +44,10 @@ struct BatchStats {
 //   bit 2  split: launches that run side by side get CTAs in proportion to
 //          their work (each a share of its full occupancy), else each is
 //          sized for the whole GPU
-constexpr uint32_t kTuneOrder = 1, kTuneMerge = 2, kTuneSplit = 4;
-constexpr uint32_t kTuneCandidates = 8;
+//   bit 3  dynamic: warps take work items from a counter as they finish
+//          (balances items of uneven cost), else static striding
+constexpr uint32_t kTuneOrder = 1, kTuneMerge = 2, kTuneSplit = 4, kTuneDynamic = 8;
+constexpr uint32_t kTuneCandidates = 16;
 // Shape of a chunk, the key of the tuning table: several kernel classes
 // (bit 0) and the bit length of the mean number of inputs per query.
 uint32_t tune_key(bool multi_class, double mean_n);
@@ -65,14 +66,17 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
 thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st, uint32_t reps,
                     double* times, uint32_t* best);
 
-// Kernel class per query for a thr_query_batch policy (thr_select.cu).
+// Counting variant per query for a thr_query_batch policy (thr_select.cu);
+// variant_flag: the THR_VARIANT_* of the flags (THR_POLICY_PLAIN).
 thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint32_t policy,
-                           uint32_t variant, std::vector<uint8_t>* cls);
+                           uint32_t variant_flag, std::vector<uint8_t>* var);
 thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
-                          const uint32_t* ids, const uint32_t* T, std::vector<uint8_t>* cls,
+                          const uint32_t* ids, const uint32_t* T, std::vector<uint8_t>* var,
                           bool* used);
 uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint32_t T);
+int variant_of_flag(uint32_t variant_flag);
+constexpr int kRuleCoeffs = 9;
 void set_rule_model(const double* c);
 void get_rule_model(double* c);
 

@@ -94,8 +94,8 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
                      uint32_t T, uint64_t* dout, uint64_t cap, uint64_t* len,
                      cudaStream_t st, bool profile, uint32_t variant) {
     const uint32_t id_off[2] = {0, n};
-    const uint8_t cls = variant == THR_VARIANT_SCANCOUNT ? uint8_t(kClassScanCount) : 0;
-    BatchInput in{1, id_off, ids, &T, &cls};
+    const uint8_t var = uint8_t(variant_of_flag(variant));
+    BatchInput in{1, id_off, ids, &T, &var};
     BatchOptions opt;
     opt.profile = profile;
     BatchStats stats;
@@ -123,17 +123,28 @@ thr_status report_error(thr_status st, const char* msg) { return fail(st, "%s", 
 
 const KernelEntry* kernel_table(int* count) {
     static const KernelEntry tab[] = {
-        {1, launch_threshold_1, occupancy_threshold_1},
-        {2, launch_threshold_2, occupancy_threshold_2},
-        {3, launch_threshold_3, occupancy_threshold_3},
-        {4, launch_threshold_4, occupancy_threshold_4},
-        {5, launch_threshold_5, occupancy_threshold_5},
-        {6, launch_threshold_6, occupancy_threshold_6},
-        {7, launch_threshold_7, occupancy_threshold_7},
-        {8, launch_threshold_8, occupancy_threshold_8},
-        {10, launch_threshold_10, occupancy_threshold_10},
-        {12, launch_threshold_12, occupancy_threshold_12},
-        {16, launch_threshold_16, occupancy_threshold_16},
+        {1, launch_threshold_1, occupancy_threshold_1, launch_threshold_pos_1,
+         occupancy_threshold_pos_1},
+        {2, launch_threshold_2, occupancy_threshold_2, launch_threshold_pos_2,
+         occupancy_threshold_pos_2},
+        {3, launch_threshold_3, occupancy_threshold_3, launch_threshold_pos_3,
+         occupancy_threshold_pos_3},
+        {4, launch_threshold_4, occupancy_threshold_4, launch_threshold_pos_4,
+         occupancy_threshold_pos_4},
+        {5, launch_threshold_5, occupancy_threshold_5, launch_threshold_pos_5,
+         occupancy_threshold_pos_5},
+        {6, launch_threshold_6, occupancy_threshold_6, launch_threshold_pos_6,
+         occupancy_threshold_pos_6},
+        {7, launch_threshold_7, occupancy_threshold_7, launch_threshold_pos_7,
+         occupancy_threshold_pos_7},
+        {8, launch_threshold_8, occupancy_threshold_8, launch_threshold_pos_8,
+         occupancy_threshold_pos_8},
+        {10, launch_threshold_10, occupancy_threshold_10, launch_threshold_pos_10,
+         occupancy_threshold_pos_10},
+        {12, launch_threshold_12, occupancy_threshold_12, launch_threshold_pos_12,
+         occupancy_threshold_pos_12},
+        {16, launch_threshold_16, occupancy_threshold_16, launch_threshold_pos_16,
+         occupancy_threshold_pos_16},
     };
     *count = int(sizeof tab / sizeof tab[0]);
     return tab;
@@ -152,8 +163,7 @@ static thr_status check_batch(const thr_index* idx, uint32_t nq, const uint32_t*
     if (policy != THR_POLICY_PLAIN && policy != THR_POLICY_RULE && policy != THR_POLICY_LEARNED)
         return fail(THR_E_INVAL, "unknown policy");
     const uint32_t variant = flags & THR_VARIANT_MASK;
-    if (variant != THR_VARIANT_CSA && variant != THR_VARIANT_SCANCOUNT)
-        return fail(THR_E_INVAL, "unknown variant");
+    if (variant_of_flag(variant) < 0) return fail(THR_E_INVAL, "unknown variant");
     for (uint32_t q = 0; q < nq; ++q) {
         if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
         const uint32_t n = id_off[q + 1] - id_off[q];
@@ -186,6 +196,17 @@ thr_status thr_rle_encode(const uint64_t* words, uint64_t nwords, uint64_t r,
     if (!out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null output");
     const int rc = encode_words(words, nwords, r, out, cap, out_len);
     if (rc == 1) return fail(THR_E_INVAL, "need ceil(r/64) words with bits >= r clear");
+    if (rc == 4) return fail(THR_E_NOSPACE, "encoded stream needs %llu words",
+                             (unsigned long long)*out_len);
+    return THR_OK;
+}
+
+thr_status thr_rle_encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r, uint64_t* out,
+                               uint64_t cap, uint64_t* out_len) {
+    if (!out_len || (cap > 0 && !out) || (nrows > 0 && !rows))
+        return fail(THR_E_INVAL, "null argument");
+    const int rc = encode_rows(rows, nrows, r, out, cap, out_len);
+    if (rc == 1) return fail(THR_E_INVAL, "rows must be ascending and below r (r >= 1)");
     if (rc == 4) return fail(THR_E_NOSPACE, "encoded stream needs %llu words",
                              (unsigned long long)*out_len);
     return THR_OK;
@@ -383,8 +404,7 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
         return fail(THR_E_INVAL, "unknown flags");
     const bool profile = flags & THR_PROFILE;
     const uint32_t variant = flags & THR_VARIANT_MASK;
-    if (variant != THR_VARIANT_CSA && variant != THR_VARIANT_SCANCOUNT)
-        return fail(THR_E_INVAL, "unknown variant");
+    if (variant_of_flag(variant) < 0) return fail(THR_E_INVAL, "unknown variant");
     for (uint32_t i = 0; i < n; ++i)
         if (ids[i] >= idx->nbitmaps)
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
@@ -416,6 +436,28 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
            "copy result");
         CK(cudaStreamSynchronize(st), "copy result");
     }
+    return THR_OK;
+}
+
+thr_status thr_select_variants(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                               const uint32_t* ids, const uint32_t* T, uint32_t flags,
+                               uint8_t* variant) {
+    if (!variant && nq) return fail(THR_E_INVAL, "null output");
+    if (nq == 0) return THR_OK;
+    if (flags & ~(THR_POLICY_MASK | THR_VARIANT_MASK)) return fail(THR_E_INVAL, "unknown flags");
+    std::vector<uint8_t> var;
+    thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &var);
+    if (ps != THR_OK) return ps;
+    for (uint32_t q = 0; q < nq; ++q) {
+        const uint32_t n = id_off[q + 1] - id_off[q];
+        variant[q] = (var[q] == kVarScanCount && n > 255) ? uint8_t(kVarCsa) : var[q];
+    }
+    return THR_OK;
+}
+
+thr_status thr_rule_model(const double* set, double* get) {
+    if (set) set_rule_model(set);
+    if (get) get_rule_model(get);
     return THR_OK;
 }
 

@@ -101,6 +101,7 @@ struct PassAParams {
     const uint32_t* list;   // slots taken by this launch
     uint32_t nlist;
     uint32_t order;   // 0 query-major, 1 subtile-major
+    uint32_t* work;   // item counter (zeroed before the launch), or null: static striding
     uint32_t W;       // uncompressed words
     uint32_t NG;      // subtiles
     uint32_t ragged;  // r % 64

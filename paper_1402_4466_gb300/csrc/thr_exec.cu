@@ -24,8 +24,9 @@ cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t s
     if (cls == kClassScanCount) return launch_scancount(p, grid, st);
     int cnt = 0;
     const KernelEntry* tab = kernel_table(&cnt);
-    if (cls < 0 || cls >= cnt) return cudaErrorInvalidValue;
-    return tab[cls].launch(p, grid, st);
+    const int w = class_width(cls);
+    if (cls < 0 || cls >= kNumClasses || w >= cnt) return cudaErrorInvalidValue;
+    return class_family(cls) == 2 ? tab[w].launch_pos(p, grid, st) : tab[w].launch(p, grid, st);
 }
 
 }  // namespace
@@ -37,13 +38,15 @@ uint64_t scratch_per_slot(uint32_t W, uint32_t NG) {
     return 4 + 32 + 2 * 32 * NB + 2 * 32 * uint64_t(NG) + 8 * uint64_t(NG) * kGW;
 }
 
-ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG) {
+ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
+                             uint64_t nlaunch) {
     const uint64_t NB = scan_blocks(NG);
     const size_t agg = sizeof(uint32_t) * kAggWords;
     ScratchLayout l{};
     l.gtick = 0;
     l.base = 8;
-    l.tick = 256;
+    l.work = 256;
+    l.tick = l.work + r256(4 * nlaunch);
     l.res = l.tick + r256(4 * Q);
     l.full = l.res + r256(16 * nq);
     l.bagg = l.full + r256(agg * Q);
@@ -75,12 +78,35 @@ void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode) {
     *zmode = z;
 }
 
+void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
+    if (v == kVarScanCount && n <= 255) {
+        *cls = kClassScanCount;
+        *zmode = 0;
+        return;
+    }
+    choose_class(n, T, cls, zmode);
+    if (v == kVarPos) {  // ones counting: the first width with 2^S > T
+        int cnt = 0;
+        const KernelEntry* tab = kernel_table(&cnt);
+        const int need = (T >= 1 && T <= n) ? bits_of(T) : 1;
+        int c = cnt - 1;
+        for (int i = 0; i < cnt; ++i)
+            if (tab[i].S >= need) {
+                c = i;
+                break;
+            }
+        *cls = kClassPos + c;
+        *zmode = 0;
+    }
+}
+
 cudaError_t class_occupancy(int cls, int* per_sm) {
     if (cls == kClassScanCount) return occupancy_scancount(per_sm);
     int cnt = 0;
     const KernelEntry* tab = kernel_table(&cnt);
-    if (cls < 0 || cls >= cnt) return cudaErrorInvalidValue;
-    return tab[cls].occupancy(per_sm);
+    const int w = class_width(cls);
+    if (cls < 0 || cls >= kNumClasses || w >= cnt) return cudaErrorInvalidValue;
+    return class_family(cls) == 2 ? tab[w].occupancy_pos(per_sm) : tab[w].occupancy(per_sm);
 }
 
 cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,
@@ -89,7 +115,8 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
                          const PassATimer* timer) {
     const ScratchLayout& l = b.lay;
     unsigned char* s = b.scratch;
-    // control words: chunk ticket, running output offset, slot tickets
+    // control words: chunk ticket, running output offset, work counters,
+    // slot tickets
     cudaError_t e = cudaMemsetAsync(s, 0, l.res, st);
     if (e != cudaSuccess) return e;
     const uint32_t NG = idx->NG;
@@ -138,6 +165,7 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
             p.list = b.lists + L.list_off;
             p.nlist = L.nlist;
             p.order = L.order;
+            p.work = L.dynamic ? reinterpret_cast<uint32_t*>(s + l.work) + ch.l0 + i : nullptr;
             const int slot = nside > 0 ? int(i % uint32_t(nside + 1)) : 0;
             cudaStream_t ls = slot == 0 ? st : aux[slot - 1];
             if ((e = launch_class(L.cls, p, std::max(L.grid, 1), ls)) != cudaSuccess) return e;

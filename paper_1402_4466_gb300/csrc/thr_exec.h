@@ -14,10 +14,18 @@
 namespace thr {
 
 // Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
-// kernel_table()[c].S, kClassScanCount the ScanCount kernel.
+// kernel_table()[c].S (grouped decode), kClassScanCount the ScanCount
+// kernel, kClassPos + c carry-save of width kernel_table()[c].S with the
+// position-major decode of mixed inputs.
 constexpr int kNumWidths = 11;
 constexpr int kClassScanCount = kNumWidths;
-constexpr int kNumClasses = kNumWidths + 1;
+constexpr int kClassPos = kNumWidths + 1;
+constexpr int kNumClasses = 2 * kNumWidths + 1;
+static_assert(kNumClasses <= 32, "class sets are 32-bit masks");
+// Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major.
+inline int class_family(int c) { return c < kNumWidths ? 0 : (c == kClassScanCount ? 1 : 2); }
+// Counter-width index of a carry-save class.
+inline int class_width(int c) { return c < kNumWidths ? c : c - kClassPos; }
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
 // chunk, work items in `order` (0 query-major, 1 subtile-major), `grid` CTAs.
@@ -27,6 +35,7 @@ struct Launch {
     uint32_t nlist;
     uint32_t order;
     int grid;
+    uint32_t dynamic;  // 1: warps take items from a counter, 0: static striding
 };
 
 // A chunk: queries q0 .. q0 + Q - 1 of the batch in slots 0 .. Q - 1, pass-A
@@ -36,11 +45,13 @@ struct ChunkPlan {
     uint32_t l0, l1;
 };
 
-// Byte offsets of the scratch regions for chunks of at most Q slots.
+// Byte offsets of the scratch regions for chunks of at most Q slots and
+// nlaunch pass-A launches in all.
 struct ScratchLayout {
-    size_t gtick, base, tick, res, full, bagg, bpref, aggs, pref, U, total;
+    size_t gtick, base, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
 };
-ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG);
+ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
+                             uint64_t nlaunch);
 // Scratch bytes per slot (everything that grows with Q).
 uint64_t scratch_per_slot(uint32_t W, uint32_t NG);
 uint32_t scan_blocks(uint32_t NG);
@@ -69,6 +80,18 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
                          const Launch* launches, const ExecBufs& b, cudaStream_t st,
                          cudaStream_t* aux, int naux, cudaEvent_t* fork_ev, int nfork_ev,
                          const PassATimer* timer);
+
+// Counting variants a query can run with (the selector's choices):
+//   kVarCsa        carry-save bit slices, inputs decoded in groups of four;
+//                  zeros of the active inputs are counted instead of ones
+//                  when that needs fewer slices
+//   kVarPos        carry-save bit slices counting ones; mixed inputs decoded
+//                  position-major (cost follows their literals)
+//   kVarScanCount  ScanCount byte counters (n <= 255; else kVarCsa runs)
+constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2;
+constexpr int kNumVariants = 3;
+// Kernel class and zero counting of a query run with variant v.
+void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 
 // Counter width and zero counting for a query of n inputs and threshold T:
 // counting ones needs 2^S > T, counting the zeros of the active inputs

@@ -10,6 +10,10 @@
 #include "../../include/thr.h"
 #include "thr_device.cuh"
 
+namespace thr {
+struct Selector;
+}
+
 struct thr_index {
     int device = 0;
     uint32_t nbitmaps = 0;
@@ -30,6 +34,8 @@ struct thr_index {
     // pass-A launch configurations chosen by thr_autotune, per batch shape
     mutable std::mutex tune_mu;
     mutable std::map<uint32_t, uint32_t> tune;
+    // cost model of THR_POLICY_LEARNED (not owned; thr_index_set_selector)
+    const thr::Selector* selector = nullptr;
 };
 
 namespace thr {

@@ -6,23 +6,27 @@
 #include "thr_launch.h"
 #include "thr_query_kernel.cuh"
 
-#define THR_DEFINE_WIDTH(S)                                                   \
-    static cudaError_t prepare_threshold_##S() {                              \
+// NAME: threshold (grouped decode) or threshold_pos (position-major decode
+// of mixed inputs).
+#define THR_DEFINE_KERNEL(S, POS, NAME)                                       \
+    static cudaError_t prepare_##NAME##_##S() {                               \
         static cudaError_t once = cudaFuncSetAttribute(                       \
-            k_threshold<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-            int(cta_smem_bytes()));                                        \
+            k_threshold<S, POS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+            int(cta_smem_bytes()));                                           \
         return once;                                                          \
     }                                                                         \
-    cudaError_t launch_threshold_##S(const PassAParams& p, int grid,          \
-                                     cudaStream_t st) {                       \
-        cudaError_t e = prepare_threshold_##S();                              \
+    cudaError_t launch_##NAME##_##S(const PassAParams& p, int grid,           \
+                                    cudaStream_t st) {                        \
+        cudaError_t e = prepare_##NAME##_##S();                               \
         if (e != cudaSuccess) return e;                                       \
-        k_threshold<S><<<grid, kNT, cta_smem_bytes(), st>>>(p);            \
+        k_threshold<S, POS><<<grid, kNT, cta_smem_bytes(), st>>>(p);          \
         return cudaGetLastError();                                            \
     }                                                                         \
-    cudaError_t occupancy_threshold_##S(int* blocks) {                        \
-        cudaError_t e = prepare_threshold_##S();                              \
+    cudaError_t occupancy_##NAME##_##S(int* blocks) {                         \
+        cudaError_t e = prepare_##NAME##_##S();                               \
         if (e != cudaSuccess) return e;                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                 \
-            blocks, k_threshold<S>, kNT, cta_smem_bytes());                \
+            blocks, k_threshold<S, POS>, kNT, cta_smem_bytes());              \
     }
+#define THR_DEFINE_WIDTH(S) THR_DEFINE_KERNEL(S, false, threshold)
+#define THR_DEFINE_WIDTH_POS(S) THR_DEFINE_KERNEL(S, true, threshold_pos)

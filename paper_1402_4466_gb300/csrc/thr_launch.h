@@ -13,8 +13,10 @@ using OccupancyFn = cudaError_t (*)(int* blocks_per_sm);
 
 struct KernelEntry {
     int S;
-    LaunchFn launch;
+    LaunchFn launch;          // grouped decode
     OccupancyFn occupancy;
+    LaunchFn launch_pos;      // position-major decode of mixed inputs
+    OccupancyFn occupancy_pos;
 };
 
 // Pass A with ScanCount counters (thr_scancount.cu): n <= 255, ones only.
@@ -25,9 +27,11 @@ cudaError_t occupancy_scancount(int* blocks_per_sm);
 // 2^S > the largest threshold its counters test.
 const KernelEntry* kernel_table(int* count);
 
-#define THR_DECLARE_WIDTH(S)                                            \
-    cudaError_t launch_threshold_##S(const PassAParams&, int, cudaStream_t); \
-    cudaError_t occupancy_threshold_##S(int*);
+#define THR_DECLARE_WIDTH(S)                                                 \
+    cudaError_t launch_threshold_##S(const PassAParams&, int, cudaStream_t);     \
+    cudaError_t occupancy_threshold_##S(int*);                                   \
+    cudaError_t launch_threshold_pos_##S(const PassAParams&, int, cudaStream_t); \
+    cudaError_t occupancy_threshold_pos_##S(int*);
 
 THR_DECLARE_WIDTH(1)
 THR_DECLARE_WIDTH(2)

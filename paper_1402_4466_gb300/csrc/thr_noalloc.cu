@@ -102,7 +102,7 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     }
     unsigned char* blk = nullptr;
     if ((e = scratch_address(dev, &blk)) != cudaSuccess) return cuda_error(e, "scratch address");
-    const ScratchLayout lay = scratch_layout(1, 1, idx->W, idx->NG);
+    const ScratchLayout lay = scratch_layout(1, 1, idx->W, idx->NG, 1);
     if (kOffScratch + lay.total > kStaticBytes)
         return report_error(THR_E_INVAL, "static scratch too small for this index");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -119,7 +119,7 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
         return cuda_error(e, "upload query");
     int per_sm = 0;
     if ((e = class_occupancy(cls, &per_sm)) != cudaSuccess) return cuda_error(e, "occupancy");
-    Launch L{cls, 0, 1, 0, 1};
+    Launch L{cls, 0, 1, 0, 1, 1};
     L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>((idx->NG + kNW - 1) / kNW,
                                                           uint64_t(std::max(per_sm, 1)) *
                                                               idx->num_sms)));

@@ -122,6 +122,91 @@ __device__ __forceinline__ void decode_group(const PassAParams& p, WarpSmem& ws,
     __syncwarp();
 }
 
+// 32 x 32 bit transpose across the warp: bit j of lane L's result is bit L
+// of lane j's x (five rounds of swapping the off-diagonal blocks).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
+    constexpr uint32_t kHi[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t sft = 16u >> k, m = kHi[k];
+        const uint32_t y = __shfl_xor_sync(~0u, x, sft);
+        x = (lane & sft) ? ((x & m) | ((y & m) >> sft)) : ((x & ~m) | ((y & ~m) << sft));
+    }
+    return x;
+}
+
+// Position-major decode of nb <= 32 mixed inputs (records rec[kCH-1-m0-j],
+// j < nb) into the counters, counting ones.  Per row, the literal and
+// ones-fill masks of the inputs are transposed so that each lane holds the
+// set of inputs with a literal (or a ones-fill word) at its own word of that
+// row; every round then takes up to four inputs from each of the lane's four
+// sets (16 loads in flight) and the warp adds them.  Rounds = the largest
+// set in the warp divided by four, not nb: sparse inputs cost their
+// literals, not a full pass each.
+template <class Count>
+__device__ __forceinline__ void pos_batch(const PassAParams& p, WarpSmem& ws, uint32_t m0,
+                                          uint32_t nb, uint32_t lane, Count& count) {
+    // stage the batch's 64-byte mask records (skipping absent ones-fill masks)
+    const uint32_t part = lane & 3;
+#pragma unroll
+    for (int k = 0; k < kMetaBatch / 8; ++k) {
+        const uint32_t j = (lane >> 2) + 8 * k;
+        if (j < nb) {
+            const uint4 rec = ws.rec[kCH - 1 - (m0 + j)];
+            if (part != 2 || ((rec.w >> 30) & 1u)) {
+                const uint4* m = reinterpret_cast<const uint4*>(
+                    p.masks + ((uint64_t(rec.y) << 32) | rec.x));
+                ws.meta[j][part] = __ldg(m + part);
+            }
+        }
+    }
+    __syncwarp();
+    const bool mine = lane < nb;
+    const uint4 myrec = mine ? ws.rec[kCH - 1 - (m0 + lane)] : make_uint4(0, 0, 0, 0);
+    const bool has_om = mine && ((myrec.w >> 30) & 1u);
+    const bool any_om = __any_sync(~0u, has_om);
+    if (mine) {  // stream index of the record's first literal into its pad words
+        const uint64_t wb = ((uint64_t(myrec.w & 0xFFu) << 32) | myrec.z) + ws.meta[lane][3].x;
+        ws.meta[lane][3].z = uint32_t(wb);
+        ws.meta[lane][3].w = uint32_t(wb >> 32);
+    }
+    uint32_t have[kRows], ones[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const uint32_t lmr = mine ? reinterpret_cast<const uint32_t*>(&ws.meta[lane][0])[r] : 0u;
+        const uint32_t omr = has_om ? reinterpret_cast<const uint32_t*>(&ws.meta[lane][2])[r] : 0u;
+        ones[r] = any_om ? transpose32(omr, lane) : 0u;
+        have[r] = transpose32(lmr, lane) | ones[r];
+    }
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    while (__any_sync(~0u, (have[0] | have[1] | have[2] | have[3]) != 0u)) {
+        uint64_t v[kGroup][kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+#pragma unroll
+            for (int k = 0; k < kGroup; ++k) {
+                v[k][r] = 0;
+                if (have[r]) {
+                    const uint32_t j = __ffs(have[r]) - 1;
+                    have[r] &= have[r] - 1u;
+                    if ((ones[r] >> j) & 1u) {
+                        v[k][r] = ~0ull;
+                    } else {
+                        const uint4 m3 = ws.meta[j][3];
+                        const uint32_t cm = reinterpret_cast<const uint32_t*>(&ws.meta[j][1])[r];
+                        const uint64_t at = ((uint64_t(m3.w) << 32) | m3.z) +
+                                            ((m3.y >> (8 * r)) & 0xFFu) + __popc(cm & lt);
+                        v[k][r] = __ldg(p.words + at);
+                    }
+                }
+            }
+        }
+        count.add(v, kGroup);
+    }
+    __syncwarp();
+}
+
 // Counting policy of the carry-save path: bit-sliced counters in registers
 // (Counters<S>), inputs added four at a time, "count >= thr" compared slice
 // by slice.
@@ -151,8 +236,10 @@ struct CsaCount {
 
 // One warp computes the 128 result words of subtile [x0, x1); lane owns rows
 // r = 0..3, words x0 + 32 r + lane (zero past x1).  Count is the counting
-// policy (carry-save bit slices, or ScanCount counters).
-template <class Count>
+// policy (carry-save bit slices, or ScanCount counters).  kPos: mixed inputs
+// go through the position-major decode (ones counting; the host never sets
+// zmode for these kernels), literal runs through the grouped one.
+template <class Count, bool kPos = false>
 __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView& q,
                                                uint32_t x0, uint32_t x1, uint32_t lane,
                                                WarpSmem& ws, Count& count,
@@ -178,7 +265,7 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
     }
     for (uint32_t c0 = 0; c0 < q.n() && !pruned; c0 += kCH) {
         const uint32_t cn = min(uint32_t(kCH), q.n() - c0);
-        uint32_t nrec = 0;
+        uint32_t nrec = 0, nrun = 0, nmix = 0;
         // 1. classify, lane per input, from the subtile descriptor
         for (uint32_t i0 = 0; i0 < cn; i0 += 32) {
             const uint32_t i = i0 + lane;
@@ -201,16 +288,40 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
                     }
                 }
             }
-            const uint32_t act = __ballot_sync(~0u, cls >= 2);
             if (one_chunk) k_ones += __popc(__ballot_sync(~0u, cls == 1));
-            if (cls >= 2) ws.rec[nrec + __popc(act & ((1u << lane) - 1u))] = r;
-            nrec += __popc(act);
+            if constexpr (kPos) {  // literal runs from the front, mixed from the back
+                const uint32_t a2 = __ballot_sync(~0u, cls == 2);
+                const uint32_t a3 = __ballot_sync(~0u, cls == 3);
+                const uint32_t below = (1u << lane) - 1u;
+                if (cls == 2) ws.rec[nrun + __popc(a2 & below)] = r;
+                if (cls == 3) ws.rec[kCH - 1 - (nmix + __popc(a3 & below))] = r;
+                nrun += __popc(a2);
+                nmix += __popc(a3);
+                nrec = nrun + nmix;
+            } else {
+                const uint32_t act = __ballot_sync(~0u, cls >= 2);
+                if (cls >= 2) ws.rec[nrec + __popc(act & ((1u << lane) - 1u))] = r;
+                nrec += __popc(act);
+            }
         }
         __syncwarp();
         if (one_chunk) {  // run-aware pruning (Sec. 6.4 cases 1 and 2)
             d_act = nrec;
             const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
             if (Tp <= 0 || Tp > int64_t(d_act)) break;
+        }
+        if constexpr (kPos) {
+            // 2'. literal runs a group at a time, mixed inputs position-major
+            for (uint32_t r0 = 0; r0 < nrun; r0 += kGroup) {
+                uint64_t v[kGroup][kRows];
+                decode_group(p, ws, r0, nrun, x0, x1, lane, v);
+                count.add(v, min(uint32_t(kGroup), nrun - r0));
+            }
+            for (uint32_t m0 = 0; m0 < nmix; m0 += 32) {
+                pos_batch(p, ws, m0, min(32u, nmix - m0), lane, count);
+                __syncwarp();
+            }
+            continue;
         }
         // 2. the active inputs into the counters, a group at a time
         for (uint32_t r0 = 0; r0 < nrec; r0 += kGroup) {
@@ -336,14 +447,15 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
 }
 
 // Pass A driver: each warp of the persistent grid takes every (grid
-// warps)-th work item of the launch, one (query, subtile) pair: query-major
+// warps)-th work item of the launch, or with a work counter the next free
+// one, an item being one (query, subtile) pair: query-major
 // (item i = query list[i / NG], subtile i % NG) or subtile-major (subtile
 // i / nlist of query list[i % nlist], so that queries sharing inputs read
 // them at about the same time).  It computes the subtile's result words with
 // the counting policy, stores them in the query's scratch words U (skipped
 // when the subtile holds one fill class only) and stores the subtile's
 // re-encoding aggregate.  No warp ever waits for another.
-template <class Count>
+template <class Count, bool kPos = false>
 __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count& count) {
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem& ws = sm.w[wid];
@@ -351,7 +463,17 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
     const uint32_t nitems = p.nlist * p.NG;
     uint32_t cur = ~0u;  // slot whose ids the warp holds
     const QView q{ws, p.ids};
-    for (uint32_t it = blockIdx.x * kNW + wid; it < nitems; it += nwarps) {
+    // static striding, or items taken from the launch's counter one at a
+    // time (the next one is requested while the current one runs)
+    uint32_t it = blockIdx.x * kNW + wid;
+    if (p.work) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(p.work, 1u);
+        it = __shfl_sync(~0u, t, 0);
+    }
+    while (it < nitems) {
+        uint32_t next = 0;
+        if (p.work && lane == 0) next = atomicAdd(p.work, 1u);
         uint32_t li, g;
         if (p.order) {
             g = it / p.nlist;
@@ -383,7 +505,7 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint64_t orow[kRows];
-        subtile_result(p, q, x0, x1, lane, ws, count, orow);
+        subtile_result<Count, kPos>(p, q, x0, x1, lane, ws, count, orow);
         // rows -> 4 consecutive words per lane (the scan's order)
 #pragma unroll
         for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
@@ -399,16 +521,18 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
             for (int r = 0; r < kRows; ++r) p.U[sg * kGW + 32 * r + lane] = orow[r];
         }
         if (lane == 0) agg_store_plain(p.aggs + sg * kAggWords, L.A);
+        it = p.work ? __shfl_sync(~0u, next, 0) : it + nwarps;
     }
 }
 
-// Pass A with the carry-save counters (S-bit saturating bit slices).
-template <int S>
+// Pass A with the carry-save counters (S-bit saturating bit slices); kPos
+// selects the position-major decode of mixed inputs.
+template <int S, bool kPos>
 __global__ void __launch_bounds__(kNT, (S <= 3 ? 8 : (S <= 6 ? 4 : 2))) k_threshold(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     CsaCount<S> count;
-    pass_a(p, sm, count);
+    pass_a<CsaCount<S>, kPos>(p, sm, count);
 }
 
 }  // namespace thr

@@ -6,46 +6,61 @@
 //                       by a linear model in the query's compressed size and
 //                       set bits, and the smallest prediction wins (the
 //                       hybrid H of Sec. 8.2).
-//   THR_POLICY_LEARNED  the learned cost model when one is loaded, else the
-//                       rule chooser.
+//   THR_POLICY_LEARNED  the learned cost model (thr_mlp.cu) attached to the
+//                       index, else the rule chooser: the variant with the
+//                       smallest predicted time wins.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
 
 #include "thr_batch.h"
+#include "thr_mlp.h"
 
 namespace thr {
 
 namespace {
 
-// Predicted pass-A time (arbitrary units) of the two counting kernels:
-//   carry-save  a0 + a1 * words + a2 * words * S
-//   ScanCount   b0 + b1 * words + b2 * set bits
-// words = compressed words of the query's inputs, S = counter width.
+// Predicted pass-A time (ms) of the three counting kernels:
+//   carry-save, grouped   a0 + a1 * words + a2 * words * S
+//   carry-save, position  c0 + c1 * words + c2 * words * S1
+//   ScanCount             b0 + b1 * words + b2 * set bits
+// words = compressed words of the query's inputs, S = counter bits of the
+// grouped kernel (the smaller of the ones and zeros counts), S1 = counter
+// bits when counting ones.  The defaults are placeholders until
+// thr_rule_model sets coefficients fitted to measured times.
 struct RuleModel {
     double a0 = 0, a1 = 1.0, a2 = 0.25;
+    double c0 = 0, c1 = 1.0, c2 = 0.3;
     double b0 = 0, b1 = 1.0, b2 = 0.35;
 };
 std::mutex g_rule_mu;
 RuleModel g_rule;
 
+int bitlen(uint64_t v) {
+    int k = 0;
+    while (v) {
+        ++k;
+        v >>= 1;
+    }
+    return k;
+}
+
 }  // namespace
 
 void set_rule_model(const double* c) {
     std::lock_guard<std::mutex> lk(g_rule_mu);
-    g_rule = RuleModel{c[0], c[1], c[2], c[3], c[4], c[5]};
+    g_rule = RuleModel{c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8]};
 }
 
 void get_rule_model(double* c) {
     std::lock_guard<std::mutex> lk(g_rule_mu);
     const RuleModel& m = g_rule;
-    const double v[6] = {m.a0, m.a1, m.a2, m.b0, m.b1, m.b2};
-    for (int i = 0; i < 6; ++i) c[i] = v[i];
+    const double v[kRuleCoeffs] = {m.a0, m.a1, m.a2, m.c0, m.c1, m.c2, m.b0, m.b1, m.b2};
+    for (int i = 0; i < kRuleCoeffs; ++i) c[i] = v[i];
 }
 
 uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint32_t T) {
-    if (n > 255) return 0;
     RuleModel m;
     {
         std::lock_guard<std::mutex> lk(g_rule_mu);
@@ -56,22 +71,36 @@ uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
         words += double(idx->desc[ids[i]].len);
         bits += double(idx->set_rows[ids[i]]);
     }
-    int cls = 0;
-    uint32_t z = 0;
-    choose_class(n, T, &cls, &z);
-    const double S = double(std::max(1, int(std::ceil(std::log2(double(std::min(T, n - T + 1)) + 1)))));
-    const double t_csa = m.a0 + m.a1 * words + m.a2 * words * S;
-    const double t_sc = m.b0 + m.b1 * words + m.b2 * bits;
-    return t_sc < t_csa ? uint8_t(kClassScanCount) : uint8_t(0);
+    const bool counted = T >= 1 && T <= n;
+    const double S1 = counted ? double(bitlen(T)) : 1.0;
+    const double S = counted ? double(std::min(bitlen(T), bitlen(uint64_t(n) - T + 1))) : 1.0;
+    const double t[3] = {m.a0 + m.a1 * words + m.a2 * words * S,
+                         m.c0 + m.c1 * words + m.c2 * words * S1,
+                         m.b0 + m.b1 * words + m.b2 * bits};
+    int best = kVarCsa;
+    for (int v = 1; v < 3; ++v) {
+        if (v == kVarScanCount && n > 255) continue;
+        if (t[v] < t[best]) best = v;
+    }
+    return uint8_t(best);
+}
+
+int variant_of_flag(uint32_t f) {
+    switch (f) {
+        case THR_VARIANT_CSA: return kVarCsa;
+        case THR_VARIANT_POSITION: return kVarPos;
+        case THR_VARIANT_SCANCOUNT: return kVarScanCount;
+        default: return -1;
+    }
 }
 
 thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint32_t policy,
-                           uint32_t variant, std::vector<uint8_t>* cls) {
-    cls->assign(nq, 0);
+                           uint32_t variant_flag, std::vector<uint8_t>* cls) {
+    cls->assign(nq, uint8_t(kVarCsa));
     if (policy == THR_POLICY_PLAIN) {
-        if (variant == THR_VARIANT_SCANCOUNT)
-            for (uint32_t q = 0; q < nq; ++q) (*cls)[q] = uint8_t(kClassScanCount);
+        const int v = variant_of_flag(variant_flag);
+        for (uint32_t q = 0; q < nq; ++q) (*cls)[q] = uint8_t(v < 0 ? kVarCsa : v);
         return THR_OK;
     }
     if (policy == THR_POLICY_LEARNED) {
@@ -84,10 +113,67 @@ thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id
     return THR_OK;
 }
 
-// Until the learned model is built the learned policy uses the rule.
-thr_status learned_choice(const thr_index*, uint32_t, const uint32_t*, const uint32_t*,
-                          const uint32_t*, std::vector<uint8_t>*, bool* used) {
+void query_features(const thr_index* idx, const uint32_t* ids, uint32_t n, uint32_t T,
+                    float* f) {
+    std::vector<double> w(n), d(n);
+    double sw = 0, sd = 0;
+    const double r = double(idx->r);
+    for (uint32_t i = 0; i < n; ++i) {
+        const double words = double(idx->desc[ids[i]].len);
+        const double dens = double(idx->set_rows[ids[i]]) / r;
+        w[i] = std::log2(words + 1.0);
+        d[i] = std::log10(dens + 1e-7);
+        sw += words;
+        sd += dens;
+    }
+    std::sort(w.begin(), w.end());
+    std::sort(d.begin(), d.end());
+    auto quant = [&](const std::vector<double>& v, double qq) {
+        const double pos = qq * double(v.size() - 1);
+        const size_t lo = size_t(pos);
+        const size_t hi = std::min(lo + 1, v.size() - 1);
+        return v[lo] + (pos - double(lo)) * (v[hi] - v[lo]);
+    };
+    f[0] = float(std::log2(double(n)));
+    f[1] = float(std::log2(double(T) + 1.0));
+    f[2] = T <= n ? float(std::log2(double(n) - double(T) + 2.0)) : 0.f;
+    f[3] = float(std::log2(r));
+    const double qs[5] = {0.0, 0.25, 0.5, 0.75, 1.0};
+    for (int k = 0; k < 5; ++k) f[4 + k] = float(quant(w, qs[k]));
+    f[9] = float(std::log2(sw + 1.0));
+    for (int k = 0; k < 5; ++k) f[10 + k] = float(quant(d, qs[k]));
+    f[15] = float(sd);
+}
+
+// With a cost model attached to the index: features of every query, one
+// forward pass for the batch, and per query the variant with the smallest
+// predicted time among those it can run (ScanCount needs n <= 255).
+thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                          const uint32_t* ids, const uint32_t* T, std::vector<uint8_t>* var,
+                          bool* used) {
+    const Selector* sel = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(idx->tune_mu);
+        sel = idx->selector;
+    }
     *used = false;
+    if (!sel) return THR_OK;
+    std::vector<float> X(size_t(nq) * kSelFeatures), Y(size_t(nq) * kSelVariants);
+    for (uint32_t q = 0; q < nq; ++q)
+        query_features(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
+                       &X[size_t(q) * kSelFeatures]);
+    thr_status s = sel->predict(X.data(), nq, Y.data());
+    if (s != THR_OK) return s;
+    for (uint32_t q = 0; q < nq; ++q) {
+        const uint32_t n = id_off[q + 1] - id_off[q];
+        int best = kVarCsa;
+        for (int v = 0; v < kSelVariants; ++v) {
+            if (v == kVarScanCount && n > 255) continue;
+            if (Y[size_t(q) * kSelVariants + v] < Y[size_t(q) * kSelVariants + best]) best = v;
+        }
+        (*var)[q] = uint8_t(best);
+    }
+    *used = true;
     return THR_OK;
 }
 

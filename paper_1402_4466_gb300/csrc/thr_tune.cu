@@ -81,8 +81,7 @@ thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st,
     for (uint32_t q = 0; q < in.nq; ++q) {
         const uint32_t n = in.id_off[q + 1] - in.id_off[q];
         uint32_t z = 0;
-        choose_class(n, in.T[q], &cls0, &z);
-        if (in.cls && in.cls[q] == kClassScanCount && n <= 255) cls0 = kClassScanCount;
+        resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls0, &z);
         present |= 1u << cls0;
         sum_n += n;
     }

@@ -18,6 +18,13 @@ Recipes (the paper's datasets are not available; these stand in for them):
 * ``many_criteria`` -- N bitmaps over r rows with densities log-uniform in
   [1e-4, 0.3]; the first half Bernoulli, the second half clustered.
 * ``plain`` -- N Bernoulli(p) bitmaps of equal density.
+* ``serving_densities`` -- Zipf(1.1) densities 0.3 k^-1.1 of the serving
+  index (odd k i.i.d., even k clustered).
+* ``similarity_densities`` / ``similarity_queries`` -- term densities
+  min(0.3, C k^-1.1) summing to the mean document length, and queries of
+  N ~ U[10, 200] Zipf-drawn terms with a planted prototype row, T = ceil(N/2).
+* ``bitmap_rows`` -- the same bitmaps as row lists (for encoders that take
+  rows, when the uncompressed words would be too large).
 
 Every generator is a pure function of its arguments (seed included).
 """
@@ -95,12 +102,13 @@ def bernoulli(seed: int, k: int, r: int, p: float) -> np.ndarray:
     return rows_to_words(bernoulli_rows(_rng(seed, 1, k), r, p), r)
 
 
-def clustered(seed: int, k: int, r: int, p: float, mean_run: float = 256.0) -> np.ndarray:
-    """Runs of ones (Geometric, mean mean_run) between Geometric gaps of mean
+def clustered_runs(seed: int, k: int, r: int, p: float, mean_run: float = 256.0):
+    """(starts, lengths) of the runs of ones of a clustered bitmap: Geometric
+    run lengths of mean mean_run between Geometric gaps of mean
     mean_run*(1-p)/p, starting with a gap."""
     rng = _rng(seed, 2, k)
     if p <= 0 or r == 0:
-        return np.zeros(nwords(r), dtype=np.uint64)
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
     mean_gap = max(mean_run * (1.0 - p) / p, 1.0)
     starts, lens = [], []
     pos = 0
@@ -117,7 +125,35 @@ def clustered(seed: int, k: int, r: int, p: float, mean_run: float = 256.0) -> n
     s = np.concatenate(starts)
     l = np.concatenate(lens)
     keep = s < r
-    return runs_to_words(s[keep], l[keep], r)
+    s, l = s[keep], l[keep]
+    return s, np.minimum(l, r - s)
+
+
+def clustered(seed: int, k: int, r: int, p: float, mean_run: float = 256.0) -> np.ndarray:
+    """Uncompressed words of the clustered bitmap of ``clustered_runs``."""
+    if p <= 0 or r == 0:
+        return np.zeros(nwords(r), dtype=np.uint64)
+    s, l = clustered_runs(seed, k, r, p, mean_run)
+    return runs_to_words(s, l, r)
+
+
+def runs_to_rows(starts: np.ndarray, lengths: np.ndarray) -> np.ndarray:
+    """Ascending rows of disjoint ascending runs [start, start + length)."""
+    if len(starts) == 0:
+        return np.zeros(0, np.int64)
+    lengths = np.asarray(lengths, np.int64)
+    total = int(lengths.sum())
+    base = np.repeat(np.asarray(starts, np.int64) - np.concatenate(([0], np.cumsum(lengths)[:-1])),
+                     lengths)
+    return base + np.arange(total, dtype=np.int64)
+
+
+def bitmap_rows(seed: int, k: int, r: int, p: float, is_clustered: bool) -> np.ndarray:
+    """Set rows (ascending) of bitmap k of a family: the same draws as
+    ``bernoulli`` / ``clustered`` with these arguments."""
+    if is_clustered:
+        return runs_to_rows(*clustered_runs(seed, k, r, p))
+    return bernoulli_rows(_rng(seed, 1, k), r, p)
 
 
 def log_uniform_densities(seed: int, n: int, lo: float = 1e-4, hi: float = 0.3) -> np.ndarray:
@@ -152,6 +188,48 @@ def many_criteria(seed: int, n: int, r: int, lo: float = 1e-4, hi: float = 0.3,
 def plain(seed: int, n: int, r: int, p: float):
     """N i.i.d. Bernoulli(p) bitmaps over r rows."""
     return [bernoulli(seed, k, r, p) for k in range(n)]
+
+
+def serving_densities(nb: int, scale: float = 0.3, s: float = 1.1) -> np.ndarray:
+    """Densities of the serving workload: bitmap k (1-based) has
+    min(0.3, scale * k^-s); odd k are i.i.d., even k clustered."""
+    k = np.arange(1, nb + 1, dtype=np.float64)
+    return np.minimum(0.3, scale * k ** -s)
+
+
+def similarity_densities(nb: int, mean_len: float = 110.0, s: float = 1.1,
+                         cap: float = 0.3) -> np.ndarray:
+    """Term densities of the similarity workload: f_k = min(cap, C k^-s)
+    with C chosen (bisection) so that the densities sum to the mean document
+    length (a document of 20..200 terms, 110 on average)."""
+    k = np.arange(1, nb + 1, dtype=np.float64)
+    lo, hi = 0.0, 1e4
+    for _ in range(200):
+        C = 0.5 * (lo + hi)
+        if np.minimum(cap, C * k ** -s).sum() < mean_len:
+            lo = C
+        else:
+            hi = C
+    return np.minimum(cap, 0.5 * (lo + hi) * k ** -s)
+
+
+def similarity_queries(seed: int, nq: int, dens: np.ndarray, r: int, nmin: int = 10,
+                       nmax: int = 200):
+    """Queries of the similarity workload: N ~ U[nmin, nmax] distinct terms
+    drawn with probability proportional to their density (Zipf weights), a
+    prototype row (uniform) planted in those N bitmaps, T = ceil(N / 2).
+    Returns (list of (ids, T), dict term -> planted rows)."""
+    rng = _rng(seed, 7)
+    w = dens / dens.sum()
+    queries, planted = [], {}
+    for _ in range(nq):
+        n = int(rng.integers(nmin, nmax + 1))
+        ids = np.sort(rng.choice(len(dens), size=n, replace=False, p=w)).astype(np.uint32)
+        row = int(rng.integers(0, r))
+        for t in ids.tolist():
+            planted.setdefault(t, []).append(row)
+        queries.append((ids, (n + 1) // 2))
+    return queries, planted
 
 
 # The two workloads run end to end on one GPU (sizes named, not numbered).

@@ -140,13 +140,13 @@ def test_batch_many_inputs_per_query(mixed):
           (rng.integers(0, 48, 200).astype(np.uint32), 1),
           (rng.integers(0, 48, 129).astype(np.uint32), 129),
           (rng.integers(0, 48, 260).astype(np.uint32), 30)]
-    for fl in (0, thr.THR_VARIANT_SCANCOUNT, thr.THR_POLICY_RULE):
+    for fl in (0, thr.THR_VARIANT_SCANCOUNT, thr.THR_VARIANT_POSITION, thr.THR_POLICY_RULE):
         off, ln, pool = thr.thr_query_batch(g, qs, flags=fl)
         _check(g, o, qs, off, ln, pool)
 
 
-@pytest.mark.parametrize("flags", [thr.THR_VARIANT_SCANCOUNT, thr.THR_POLICY_RULE,
-                                   thr.THR_POLICY_LEARNED])
+@pytest.mark.parametrize("flags", [thr.THR_VARIANT_SCANCOUNT, thr.THR_VARIANT_POSITION,
+                                   thr.THR_POLICY_RULE, thr.THR_POLICY_LEARNED])
 def test_batch_policies(mixed, flags):
     g, o, r = mixed
     qs = _queries(9, 48, 30)
@@ -177,10 +177,10 @@ def test_batch_many_criteria_full_size(many_criteria_full):
     _check(g, o, qs, off, ln, pool)
 
 
-@pytest.mark.parametrize("cfg", range(8))
+@pytest.mark.parametrize("cfg", range(16))
 def test_every_launch_configuration(mixed, monkeypatch, cfg):
-    """Work order, class merging and grid split change only the schedule:
-    every configuration gives the oracle's results."""
+    """Work order, class merging, grid split and dynamic work fetch change
+    only the schedule: every configuration gives the oracle's results."""
     g, o, r = mixed
     monkeypatch.setenv("THR_TUNE_CONFIG", str(cfg))
     qs = _queries(20 + cfg, 48, 24, nmax=300)
@@ -194,7 +194,7 @@ def test_autotune_keeps_the_fastest(mixed):
     qs = _queries(30, 48, 16)
     before = thr.thr_query_batch(g, qs)
     best, times = thr.thr_autotune(g, qs, reps=2)
-    assert 0 <= best < 8 and len(times) == 8 and all(t > 0 for t in times)
+    assert 0 <= best < 16 and len(times) == 16 and all(t > 0 for t in times)
     assert times[best] == min(times)
     off, ln, pool = thr.thr_query_batch(g, qs)
     assert thr.thr_last_batch_info()["config"] == best

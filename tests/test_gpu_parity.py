@@ -231,3 +231,40 @@ def test_scancount_many_criteria_full_size(many_criteria_full):
     p = Pair(words, r)
     for T in (2, 16):
         p.check(list(range(synth.MANY_N)), T, SC)
+
+
+# ---- carry-save counters with the position-major decode of mixed inputs
+
+POS = thr.THR_VARIANT_POSITION
+
+
+def test_position_random_tiny_all_thresholds():
+    rng = np.random.default_rng(303)
+    for _ in range(20):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 4096, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        for T in range(0, n + 2):
+            p.check(list(range(n)), T, POS)
+
+
+def test_position_clustered_runs_and_chunks():
+    """Clustered bitmaps put ones-fill words inside mixed subtiles; more
+    than 32 mixed inputs per subtile take several transposed batches, more
+    than 128 inputs several record chunks."""
+    r = (1 << 18) + 1234
+    words, _ = synth.many_criteria(13, 40, r)
+    p = Pair(words, r)
+    for T in (1, 2, 3, 7, 20, 39, 40, 41):
+        p.check(list(range(40)), T, POS)
+    rng = np.random.default_rng(14)
+    ids = rng.integers(0, 40, size=300).tolist()
+    for T in (1, 5, 60, 150, 299):
+        p.check(ids, T, POS)
+
+
+def test_position_many_criteria_full_size(many_criteria_full):
+    words, r = many_criteria_full
+    p = Pair(words, r)
+    for T in (*synth.MANY_TS, 1, 64):
+        p.check(list(range(synth.MANY_N)), T, POS)
