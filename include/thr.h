@@ -35,9 +35,9 @@
  *
  * Errors: every call returns a thr_status; no C++ exception crosses the ABI.
  * thr_last_error() describes the last failure of the calling thread.
- * A CUDA failure returns THR_E_CUDA; a device-side wait that exceeded its
- * iteration limit returns THR_E_TIMEOUT (the result is then undefined, the
- * CUDA context stays usable).
+ * A CUDA failure returns THR_E_CUDA.  No kernel of the library waits on
+ * another CTA or launch (cross-CTA scans finish in the last CTA to arrive),
+ * so THR_E_TIMEOUT is reserved and not returned.
  */
 #ifndef THR_H
 #define THR_H
@@ -57,7 +57,7 @@ typedef enum {
     THR_E_NOMEM = 3,   /* host or device allocation failed */
     THR_E_NOSPACE = 4, /* output buffer too small; required size returned */
     THR_E_CUDA = 5,    /* a CUDA runtime call failed */
-    THR_E_TIMEOUT = 6  /* a device wait hit its iteration limit */
+    THR_E_TIMEOUT = 6  /* reserved (no device-side waits) */
 } thr_status;
 
 /* flags for thr_query / thr_query_batch */

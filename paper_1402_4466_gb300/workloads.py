@@ -63,9 +63,10 @@ def serving(nb: int = 1 << 14, r: int = 1 << 26, seed: int = 0, workers: int = 0
 
 def similarity(nb: int = 1 << 16, r: int = 1 << 24, nq: int = 4096, seed: int = 0,
                workers: int = 0):
-    """(words, offsets, r, queries) of the similarity index and its batch."""
+    """(words, offsets, r, queries, prototype rows) of the similarity index
+    and its batch."""
     dens = synth.similarity_densities(nb)
-    queries, planted = synth.similarity_queries(seed, nq, dens, r)
+    queries, planted, protos = synth.similarity_queries(seed, nq, dens, r)
     jobs = [(seed, k, r, float(dens[k]), False, planted.get(k)) for k in range(nb)]
     words, offsets = encode_family(jobs, workers)
-    return words, offsets, r, queries
+    return words, offsets, r, queries, protos

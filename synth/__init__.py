@@ -218,10 +218,11 @@ def similarity_queries(seed: int, nq: int, dens: np.ndarray, r: int, nmin: int =
     """Queries of the similarity workload: N ~ U[nmin, nmax] distinct terms
     drawn with probability proportional to their density (Zipf weights), a
     prototype row (uniform) planted in those N bitmaps, T = ceil(N / 2).
-    Returns (list of (ids, T), dict term -> planted rows)."""
+    Returns (list of (ids, T), dict term -> planted rows, prototype row of
+    every query)."""
     rng = _rng(seed, 7)
     w = dens / dens.sum()
-    queries, planted = [], {}
+    queries, planted, protos = [], {}, []
     for _ in range(nq):
         n = int(rng.integers(nmin, nmax + 1))
         ids = np.sort(rng.choice(len(dens), size=n, replace=False, p=w)).astype(np.uint32)
@@ -229,7 +230,8 @@ def similarity_queries(seed: int, nq: int, dens: np.ndarray, r: int, nmin: int =
         for t in ids.tolist():
             planted.setdefault(t, []).append(row)
         queries.append((ids, (n + 1) // 2))
-    return queries, planted
+        protos.append(row)
+    return queries, planted, protos
 
 
 # The two workloads run end to end on one GPU (sizes named, not numbered).
