@@ -224,6 +224,23 @@ thr_status idx_info(const thr_index *idx, uint32_t *nbitmaps, uint64_t *r,
 thr_status thr_rle_encode(const uint64_t *words, uint64_t nwords, uint64_t r,
                           uint64_t *out, uint64_t cap, uint64_t *out_len);
 thr_status thr_rle_validate(const uint64_t *stream, uint64_t len, uint64_t r);
+/*
+ * Row-range sharding (host).  thr_rle_slice writes the canonical stream of
+ * the uncompressed words [w0, w1) (rows 64 w0 .. 64 w1 - 1) of a canonical
+ * stream of an r-row bitmap: a shard of the rows.  thr_rle_stitch writes the
+ * canonical stream of the concatenation of nparts streams of consecutive
+ * row ranges (part k covers rows[k] rows, a multiple of 64 except for the
+ * last part): a fill that continues a fill of the same value across a seam
+ * and literals that follow literals merge into one group, so the threshold
+ * results of the shards of a row-sharded index stitch into the result of the
+ * whole.  Both validate their inputs (THR_E_FORMAT) and return
+ * THR_E_NOSPACE with the needed length when cap is too small.
+ */
+thr_status thr_rle_slice(const uint64_t *stream, uint64_t len, uint64_t r, uint64_t w0,
+                         uint64_t w1, uint64_t *out, uint64_t cap, uint64_t *out_len);
+thr_status thr_rle_stitch(const uint64_t *const *parts, const uint64_t *lens,
+                          const uint64_t *rows, uint32_t nparts, uint64_t *out,
+                          uint64_t cap, uint64_t *out_len);
 /* The canonical stream of the r-row bitmap whose set rows are
  * rows[0..nrows) (ascending, repeats allowed, each < r), written like
  * thr_rle_encode but without forming the uncompressed words.  Host-only. */

@@ -40,6 +40,7 @@ ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_stati
                "thr_selector_predict", "thr_selector_gradients", "thr_query_features",
                "thr_index_set_selector", "thr_server_create", "thr_server_submit",
                "thr_server_wait", "thr_server_stats", "thr_server_free", "thr_rle_encode_rows",
+               "thr_rle_slice", "thr_rle_stitch",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -77,6 +78,8 @@ def load():
             lib.thr_rle_encode.argtypes = [vp, u64, u64, vp, u64, u64p]
             lib.thr_rle_validate.argtypes = [vp, u64, u64]
             lib.thr_rle_encode_rows.argtypes = [vp, u64, u64, vp, u64, u64p]
+            lib.thr_rle_slice.argtypes = [vp, u64, u64, u64, u64, vp, u64, u64p]
+            lib.thr_rle_stitch.argtypes = [vp, vp, vp, u32, vp, u64, u64p]
             lib.thr_last_error.argtypes = []
             lib.thr_last_error.restype = ctypes.c_char_p
             lib.thr_last_kernel_ms.argtypes = []
@@ -112,7 +115,8 @@ def load():
                       "thr_selector_set_norm", "thr_selector_train", "thr_selector_predict",
                       "thr_selector_gradients", "thr_query_features", "thr_index_set_selector",
                       "thr_server_create", "thr_server_submit", "thr_server_wait",
-                      "thr_server_stats", "thr_rle_encode_rows"):
+                      "thr_server_stats", "thr_rle_encode_rows", "thr_rle_slice",
+                      "thr_rle_stitch"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -333,6 +337,33 @@ def thr_rle_encode_rows(rows, r: int) -> np.ndarray:
     _check(load().thr_rle_encode_rows(ctypes.c_void_p(rows.ctypes.data if rows.size else 0),
                                       rows.size, int(r), ctypes.c_void_p(out.ctypes.data),
                                       out.size, ctypes.byref(n)), "thr_rle_encode_rows")
+    return out[: n.value].copy()
+
+
+def thr_rle_slice(stream, r: int, w0: int, w1: int) -> np.ndarray:
+    """Canonical stream of the words [w0, w1) of a canonical stream."""
+    s = _u64(stream)
+    out = np.empty(min(2 * s.size + 2, w1 - w0 + 1), dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(load().thr_rle_slice(ctypes.c_void_p(s.ctypes.data), s.size, int(r), int(w0), int(w1),
+                                ctypes.c_void_p(out.ctypes.data), out.size, ctypes.byref(n)),
+           "thr_rle_slice")
+    return out[: n.value].copy()
+
+
+def thr_rle_stitch(parts, rows) -> np.ndarray:
+    """Canonical stream of consecutive row-range parts (rows[k] rows each)."""
+    parts = [_u64(p) for p in parts]
+    rows = np.ascontiguousarray(rows, dtype=np.uint64)
+    ptrs = (ctypes.c_void_p * len(parts))(*[p.ctypes.data for p in parts])
+    lens = np.array([p.size for p in parts], dtype=np.uint64)
+    cap = int(sum(p.size for p in parts)) + 1
+    out = np.empty(cap, dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(load().thr_rle_stitch(ptrs, ctypes.c_void_p(lens.ctypes.data),
+                                 ctypes.c_void_p(rows.ctypes.data), len(parts),
+                                 ctypes.c_void_p(out.ctypes.data), out.size, ctypes.byref(n)),
+           "thr_rle_stitch")
     return out[: n.value].copy()
 
 

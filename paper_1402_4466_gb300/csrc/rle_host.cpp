@@ -137,6 +137,49 @@ struct GroupEncoder {
 
 }  // namespace
 
+// Feeds the uncompressed words [w0, w1) of a canonical stream s (W words)
+// into g as fills and literals.
+void feed_range(const uint64_t* s, uint64_t len, uint64_t w0, uint64_t w1, GroupEncoder* g) {
+    uint64_t pos = 0;  // uncompressed word where the current group starts
+    for (uint64_t i = 0; i < len && pos < w1;) {
+        const uint64_t m = s[i];
+        const uint64_t F = marker_fill_len(m), L = marker_lit_count(m), b = marker_fill_bit(m);
+        // fill words [pos, pos + F)
+        const uint64_t f0 = std::max(pos, w0), f1 = std::min(pos + F, w1);
+        if (f1 > f0) g->fill(F ? b : 0, f1 - f0);
+        pos += F;
+        // literal words [pos, pos + L)
+        const uint64_t l0 = std::max(pos, w0), l1 = std::min(pos + L, w1);
+        for (uint64_t w = l0; w < l1; ++w) g->literal(s[i + 1 + (w - pos)]);
+        pos += L;
+        i += 1 + L;
+    }
+}
+
+int slice_stream(const uint64_t* s, uint64_t len, uint64_t r, uint64_t w0, uint64_t w1,
+                 uint64_t* out, uint64_t cap, uint64_t* out_len) {
+    const uint64_t W = (r + 63) / 64;
+    if (w0 >= w1 || w1 > W) return 1;
+    GroupEncoder g{Emitter{out, cap}};
+    feed_range(s, len, w0, w1, &g);
+    g.flush();
+    *out_len = g.e.n;
+    return g.e.n <= cap ? 0 : 4;
+}
+
+int stitch_streams(const uint64_t* const* parts, const uint64_t* lens, const uint64_t* words,
+                   uint32_t nparts, uint64_t* out, uint64_t cap, uint64_t* out_len) {
+    if (nparts == 0) return 1;
+    GroupEncoder g{Emitter{out, cap}};
+    for (uint32_t k = 0; k < nparts; ++k) {
+        if (!words[k]) return 1;
+        feed_range(parts[k], lens[k], 0, words[k], &g);
+    }
+    g.flush();
+    *out_len = g.e.n;
+    return g.e.n <= cap ? 0 : 4;
+}
+
 int encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r, uint64_t* out, uint64_t cap,
                 uint64_t* out_len) {
     const uint64_t W = (r + 63) / 64;

@@ -46,4 +46,18 @@ int encode_words(const uint64_t* words, uint64_t nwords, uint64_t r,
 int encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r, uint64_t* out, uint64_t cap,
                 uint64_t* out_len);
 
+// The uncompressed words [w0, w1) of the canonical stream s of an r-row
+// bitmap, as a canonical stream of its own (a row-range shard when w0 and w1
+// are word boundaries).  The stream must be valid (scan_stream).  Returns 0,
+// 1 (bad range) or 4 (out too small; *out_len still receives the length).
+int slice_stream(const uint64_t* s, uint64_t len, uint64_t r, uint64_t w0, uint64_t w1,
+                 uint64_t* out, uint64_t cap, uint64_t* out_len);
+
+// The canonical stream of the concatenation of nparts valid canonical
+// streams covering words[k] uncompressed words each: runs that meet at a
+// seam merge (a fill continuing a fill of the same value, literals following
+// literals).  Returns 0, 1 (bad argument) or 4 (out too small).
+int stitch_streams(const uint64_t* const* parts, const uint64_t* lens, const uint64_t* words,
+                   uint32_t nparts, uint64_t* out, uint64_t cap, uint64_t* out_len);
+
 }  // namespace thr

@@ -212,6 +212,43 @@ thr_status thr_rle_encode_rows(const uint64_t* rows, uint64_t nrows, uint64_t r,
     return THR_OK;
 }
 
+thr_status thr_rle_slice(const uint64_t* stream, uint64_t len, uint64_t r, uint64_t w0,
+                         uint64_t w1, uint64_t* out, uint64_t cap, uint64_t* out_len) {
+    if (!stream || !out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null argument");
+    if ((r + 63) / 64 > kMaxWords) return fail(THR_E_INVAL, "r too large");
+    StreamScan sc;
+    std::string why;
+    if (scan_stream(stream, len, r, &sc, &why) != 0)
+        return fail(THR_E_FORMAT, "%s", why.c_str());
+    const int rc = slice_stream(stream, len, r, w0, w1, out, cap, out_len);
+    if (rc == 1) return fail(THR_E_INVAL, "need w0 < w1 <= ceil(r/64)");
+    if (rc == 4) return fail(THR_E_NOSPACE, "slice needs %llu words", (unsigned long long)*out_len);
+    return THR_OK;
+}
+
+thr_status thr_rle_stitch(const uint64_t* const* parts, const uint64_t* lens,
+                          const uint64_t* rows, uint32_t nparts, uint64_t* out, uint64_t cap,
+                          uint64_t* out_len) {
+    if (!parts || !lens || !rows || !out_len || (cap > 0 && !out))
+        return fail(THR_E_INVAL, "null argument");
+    if (nparts == 0) return fail(THR_E_INVAL, "no parts");
+    std::vector<uint64_t> words(nparts);
+    for (uint32_t k = 0; k < nparts; ++k) {
+        if (rows[k] == 0 || (k + 1 < nparts && rows[k] % 64 != 0))
+            return fail(THR_E_INVAL, "part %u: rows must be positive, a multiple of 64 but the last", k);
+        StreamScan sc;
+        std::string why;
+        if (scan_stream(parts[k], lens[k], rows[k], &sc, &why) != 0)
+            return fail(THR_E_FORMAT, "part %u: %s", k, why.c_str());
+        words[k] = (rows[k] + 63) / 64;
+    }
+    const int rc = stitch_streams(parts, lens, words.data(), nparts, out, cap, out_len);
+    if (rc == 1) return fail(THR_E_INVAL, "bad parts");
+    if (rc == 4) return fail(THR_E_NOSPACE, "stitched stream needs %llu words",
+                             (unsigned long long)*out_len);
+    return THR_OK;
+}
+
 thr_status thr_rle_validate(const uint64_t* stream, uint64_t len, uint64_t r) {
     if (!stream && len) return fail(THR_E_INVAL, "null stream");
     if ((r + 63) / 64 > kMaxWords) return fail(THR_E_INVAL, "r too large");

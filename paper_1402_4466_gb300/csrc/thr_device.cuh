@@ -203,6 +203,13 @@ struct Counters {
         if constexpr (S > 2) add1<2>(h, k3);
         else sticky[h] |= k3;
     }
+    // add two 1-bit inputs: one full adder at weight 1, then ripple the
+    // weight-2 carry
+    __device__ __forceinline__ void add_pair(int h, uint32_t a, uint32_t b) {
+        const uint32_t k1 = add2<0>(h, a, b);
+        if constexpr (S > 1) add1<1>(h, k1);
+        else sticky[h] |= k1;
+    }
     // bit-sliced "count >= thr" (thr < 2^S), most significant slice first
     __device__ __forceinline__ uint32_t ge(int h, uint32_t thr) const {
         uint32_t eq = ~0u, gt = 0u;

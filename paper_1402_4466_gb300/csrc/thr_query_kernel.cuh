@@ -210,6 +210,8 @@ __device__ __forceinline__ void pos_batch(const PassAParams& p, WarpSmem& ws, ui
 // Counting policy of the carry-save path: bit-sliced counters in registers
 // (Counters<S>), inputs added four at a time, "count >= thr" compared slice
 // by slice.
+static_assert(kGroup == 2 || kGroup == 4, "inputs are added in fours or twos");
+
 template <int S>
 struct CsaCount {
     Counters<S> cnt;
@@ -217,10 +219,15 @@ struct CsaCount {
     __device__ __forceinline__ void add(const uint64_t (&v)[kGroup][kRows], uint32_t) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            cnt.add4(2 * r, uint32_t(v[0][r]), uint32_t(v[1][r]), uint32_t(v[2][r]),
-                     uint32_t(v[3][r]));
-            cnt.add4(2 * r + 1, uint32_t(v[0][r] >> 32), uint32_t(v[1][r] >> 32),
-                     uint32_t(v[2][r] >> 32), uint32_t(v[3][r] >> 32));
+            if constexpr (kGroup == 4) {
+                cnt.add4(2 * r, uint32_t(v[0][r]), uint32_t(v[1][r]), uint32_t(v[2][r]),
+                         uint32_t(v[3][r]));
+                cnt.add4(2 * r + 1, uint32_t(v[0][r] >> 32), uint32_t(v[1][r] >> 32),
+                         uint32_t(v[2][r] >> 32), uint32_t(v[3][r] >> 32));
+            } else {
+                cnt.add_pair(2 * r, uint32_t(v[0][r]), uint32_t(v[1][r]));
+                cnt.add_pair(2 * r + 1, uint32_t(v[0][r] >> 32), uint32_t(v[1][r] >> 32));
+            }
         }
     }
     // thr >= 1; flip inverts the result (counting zeros)
