@@ -9,12 +9,15 @@ the four queries over all 64 bitmaps at T = 2, 16, 32 and 63.
 
 Reported (one JSON line from rank 0):
   value         queries/s over the timed steps, index resident in HBM, output
-                into a device buffer; L2 is flushed (256 MiB write, untimed)
-                before every query, each query timed with CUDA events
+                into a device pool; one step = the four queries as one
+                thr_query_batch call (CUDA graph, autotuned launch, learned
+                variant policy), timed with CUDA events around the call; L2 is
+                flushed (256 MiB write, untimed) before every step
+  plain         the same queries as one thr_query call each
   input_gbs     compressed input bytes / time (Sec. 7 of the paper measures
                 throughput as input bytes over time)
-  e2e           the same queries through the C ABI with host ids and a host
-                output buffer (the result copied back inside the timed call)
+  e2e           the same batch through the C ABI with host ids and a host
+                result pool (the results copied back inside the timed call)
   roofline      the query kernel: algorithmic bytes (compressed input read +
                 compressed output written) per launch / its event-timed
                 duration, against the measured HBM copy bandwidth
@@ -176,6 +179,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import paper_1402_4466_gb300 as thr
+    from paper_1402_4466_gb300 import selector_weights
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -188,24 +192,49 @@ def run_ours(args):
     build_s = time.perf_counter() - t0
     ids = np.arange(synth.MANY_N, dtype=np.uint32)
     Ts = list(synth.MANY_TS)
+    qs = [(ids, T) for T in Ts]
     in_bytes = 8 * int(goff[-1])  # every query reads all 64 streams
     W = idx.nwords
     dout = torch.empty(W + 1, dtype=torch.int64, device="cuda")
+    pool = torch.empty(len(Ts) * (W + 1), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    POLICY = thr.THR_POLICY_LEARNED
+    sel = selector_weights.attach(idx)  # the shipped cost model (and refit rule)
+
+    def flushed():
+        with torch.cuda.stream(stream):
+            flush.zero_()  # write 256 MiB > L2 before every timed call (untimed)
+        stream.synchronize()
+
     out_words = {}
 
-    def one_query(T, timed):
-        with torch.cuda.stream(stream):
-            flush.zero_()  # write 256 MiB > L2 before every query (untimed)
-        stream.synchronize()
+    def batched_step():
+        """The step's four queries as one thr_query_batch call (CUDA graph,
+        autotuned launch, learned variant policy); CUDA events on the
+        caller's stream around the synchronous call."""
+        flushed()
         ev0.record(stream)
-        n = thr.thr_query(idx, ids, T, out=dout, flags=thr.THR_PROFILE, stream=stream)
+        off, ln, _ = thr.thr_query_batch(idx, qs, pool=pool, flags=POLICY, stream=stream)
         ev1.record(stream)
         ev1.synchronize()
-        out_words[T] = n
+        for T, n in zip(Ts, ln):
+            out_words[T] = int(n)
+        return ev0.elapsed_time(ev1)
+
+    def plain_query(T, flags=0):
+        flushed()
+        ev0.record(stream)
+        n = thr.thr_query(idx, ids, T, out=dout, flags=flags | thr.THR_PROFILE, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        out_words[T] = int(n)
         return ev0.elapsed_time(ev1), thr.thr_last_kernel_ms()
+
+    # launch configurations of this workload's shapes (autotuner)
+    single_cfg, single_tune_ms = thr.thr_autotune(idx, [qs[0]], reps=3, stream=stream)
+    batch_cfg, batch_tune_ms = thr.thr_autotune(idx, qs, flags=POLICY, reps=3, stream=stream)
 
     uuid = None
     try:
@@ -213,110 +242,63 @@ def run_ours(args):
     except Exception:
         uuid = None
     clocks = ClockSampler(uuid)  # from the warm-up on, so that it has samples under load
-    # launch configuration of single queries of this shape (autotuner)
-    single_cfg, single_tune_ms = thr.thr_autotune(idx, [(ids, Ts[0])], reps=3, stream=stream)
     for _ in range(args.warmup):
+        batched_step()
         for T in Ts:
-            one_query(T, False)
+            plain_query(T)
     clocks.wait_first()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    q_ms, k_ms, k_bytes = [], [], []
-    for _ in range(args.steps):
-        for T in Ts:
-            qm, km = one_query(T, True)
-            q_ms.append(qm)
-            k_ms.append(km)
-            k_bytes.append(in_bytes + 8 * out_words[T])
+    b_ms = [batched_step() for _ in range(args.steps)]
+    binfo = thr.thr_last_batch_info()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    total_ms = sum(q_ms)
+    total_ms = sum(b_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    nq = len(q_ms) * world
+    nq = len(Ts) * args.steps * world
     value = nq / (total_ms / 1e3)
     input_gbs = (in_bytes * nq) / (total_ms / 1e3) / 1e9
 
-    # pass-A time of each counting variant on the step's queries (events,
-    # L2 flushed before each query)
+    # plain: one thr_query per query (default variant), and the pass-A
+    # kernel time of each (the roofline's launch)
+    q_ms, k_ms, k_bytes = [], [], []
+    for _ in range(args.steps):
+        for T in Ts:
+            qm, km = plain_query(T)
+            q_ms.append(qm)
+            k_ms.append(km)
+            k_bytes.append(in_bytes + 8 * out_words[T])
+    plain_value = len(q_ms) / (sum(q_ms) / 1e3)
     variant_ms = {}
     for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("position", thr.THR_VARIANT_POSITION),
                          ("scancount", thr.THR_VARIANT_SCANCOUNT)):
         per_t = {}
         for T in Ts:
-            ts = []
-            for _ in range(max(args.steps, 3)):
-                with torch.cuda.stream(stream):
-                    flush.zero_()
-                stream.synchronize()
-                thr.thr_query(idx, ids, T, out=dout, flags=vflag | thr.THR_PROFILE, stream=stream)
-                ts.append(thr.thr_last_kernel_ms())
+            ts = [plain_query(T, vflag)[1] for _ in range(max(args.steps, 3))]
             per_t[str(T)] = round(statistics.median(ts), 5)
         variant_ms[vname] = per_t
-
-    # batched: the step's queries as one thr_query_batch call, replayed as a
-    # CUDA graph, with the launch configuration the autotuner picks; timed on
-    # the host clock around the synchronous call, beside the plain per-query
-    # calls timed the same way (L2 flushed before each call)
-    qs = [(ids, T) for T in Ts]
-    pool = torch.empty(len(Ts) * (W + 1), dtype=torch.int64, device="cuda")
-    tune_best, tune_ms = thr.thr_autotune(idx, qs, reps=3, stream=stream)
-
-    def wall(fn):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        stream.synchronize()
-        t1 = time.perf_counter()
-        fn()
-        return (time.perf_counter() - t1) * 1e3
-
-    def batch_call():
-        thr.thr_query_batch(idx, qs, pool=pool, stream=stream)
-
-    def plain_calls():
-        for T in Ts:
-            thr.thr_query(idx, ids, T, out=dout, stream=stream)
-
-    for _ in range(args.warmup):
-        wall(batch_call)
-        wall(plain_calls)
-    b_ms = [wall(batch_call) for _ in range(args.steps)]
-    binfo = thr.thr_last_batch_info()
-    p_ms = [wall(plain_calls) for _ in range(args.steps)]
     clk = clocks.stop()
-    batched = {
-        "value": round(len(Ts) * args.steps / (sum(b_ms) / 1e3), 3),
-        "unit": "queries/s",
-        "plain_same_clock": round(len(Ts) * args.steps / (sum(p_ms) / 1e3), 3),
-        "clock": "host wall time around each synchronous call",
-        "launch_config": binfo["config"],
-        "graph_replayed": binfo["graph"] == 1,
-        "pass_a_launches": binfo["launches"],
-        "autotune_ms": [round(t, 4) for t in tune_ms],
-    }
-    batched["speedup_vs_plain"] = round(batched["value"] / batched["plain_same_clock"], 3)
 
-    # end to end through the C ABI: host ids in, host result out
+    # end to end through the C ABI: host ids in, host result pool out
     e2e_ms, d2h = [], 0
     for _ in range(args.steps):
-        for T in Ts:
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            stream.synchronize()
-            t1 = time.perf_counter()
-            res = thr.thr_query(idx, ids, T, stream=stream)
-            e2e_ms.append((time.perf_counter() - t1) * 1e3)
-            d2h += 8 * len(res) + 16
-    e2e_value = len(e2e_ms) / (sum(e2e_ms) / 1e3)
+        flushed()
+        t1 = time.perf_counter()
+        off, ln, hp = thr.thr_query_batch(idx, qs, flags=POLICY, stream=stream)
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+        d2h += 8 * int(ln.sum()) + 16 * len(Ts)
+    e2e_value = len(Ts) * len(e2e_ms) / (sum(e2e_ms) / 1e3)
 
     peak, peak_kind = measured_peaks()
     avg_bytes = statistics.mean(k_bytes)
     avg_kms = statistics.mean(k_ms)
     achieved = avg_bytes / (avg_kms / 1e3) / 1e9
+    launches_per_step = binfo["launches"] + 2 * binfo["chunks"]
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -338,28 +320,38 @@ def run_ours(args):
             "thresholds": Ts,
             "compressed_input_bytes_per_query": in_bytes,
             "output_words": {str(k): int(v) for k, v in out_words.items()},
-            "l2": "flushed before every query (256 MiB device write, untimed)",
+            "step": "the four queries as one thr_query_batch call: CUDA graph replay, "
+                    "autotuned launch, learned variant policy (shipped cost model)",
+            "l2": "flushed before every timed call (256 MiB device write, untimed)",
             "parallelism": f"replicas x{world}",
             "index_build_s": round(build_s, 3),
         },
         "e2e": {"value": round(e2e_value, 3), "unit": "queries/s",
-                "h2d_bytes_per_step": 4 * len(ids) * len(Ts),
+                "h2d_bytes_per_step": 4 * len(ids) * len(Ts) + 8 * (len(Ts) + 1),
                 "d2h_bytes_per_step": d2h // max(args.steps, 1)},
+        "plain": {"value": round(plain_value, 3), "unit": "queries/s",
+                  "what": "one thr_query per query, default variant, CUDA events per call",
+                  "batched_speedup": round(value / plain_value, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(), "peak_kind": peak_kind,
                      "kernel": "k_threshold", "bytes_per_launch": int(avg_bytes),
-                     "kernel_ms": round(avg_kms, 5), "launch_config": single_cfg,
-                     "autotune_ms": [round(t, 4) for t in single_tune_ms]},
-        "batched": batched,
+                     "kernel_ms": round(avg_kms, 5), "launch_config": single_cfg},
+        "batched": {"launch_config": binfo["config"], "graph_replayed": binfo["graph"] == 1,
+                    "pass_a_launches": binfo["launches"], "chunks": binfo["chunks"],
+                    "variants": thr.select_variants(idx, qs, POLICY).tolist(),
+                    "autotune_ms": [round(t, 4) for t in batch_tune_ms],
+                    "single_query_autotune_ms": [round(t, 4) for t in single_tune_ms]},
         "pass_a_ms_by_variant": variant_ms,
-        "gpu_launches": 3 * len(q_ms),  # passes A, B and C per query
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(gw, goff, r, ids, Ts, idx, thr)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    thr.set_selector(idx, None)
+    del sel
     idx.close()
     if world > 1:
         dist.destroy_process_group()

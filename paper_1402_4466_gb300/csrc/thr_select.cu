@@ -145,6 +145,8 @@ void query_features(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
     f[15] = float(sd);
 }
 
+constexpr float kSwitchGain = 0.10f;
+
 // With a cost model attached to the index: features of every query, one
 // forward pass for the batch, and per query the variant with the smallest
 // predicted time among those it can run (ScanCount needs n <= 255).
@@ -164,12 +166,21 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
                        &X[size_t(q) * kSelFeatures]);
     thr_status s = sel->predict(X.data(), nq, Y.data());
     if (s != THR_OK) return s;
+    // another variant replaces the default only when it is predicted at
+    // least kSwitchGain faster: a marginal switch costs a batch an extra
+    // launch and the sharing of reads with the default's queries
+    const float margin = std::log(1.0f + kSwitchGain);
     for (uint32_t q = 0; q < nq; ++q) {
         const uint32_t n = id_off[q + 1] - id_off[q];
+        const float* y = &Y[size_t(q) * kSelVariants];
         int best = kVarCsa;
+        float best_y = y[kVarCsa] - margin;
         for (int v = 0; v < kSelVariants; ++v) {
-            if (v == kVarScanCount && n > 255) continue;
-            if (Y[size_t(q) * kSelVariants + v] < Y[size_t(q) * kSelVariants + best]) best = v;
+            if (v == kVarCsa || (v == kVarScanCount && n > 255)) continue;
+            if (y[v] < best_y) {
+                best = v;
+                best_y = y[v];
+            }
         }
         (*var)[q] = uint8_t(best);
     }

@@ -219,15 +219,15 @@ def main():
     coeffs = fit_rule(train, indexes)
     thr.rule_model(coeffs)
 
-    # choices on the held-out queries
-    pred = sel.predict(Xte)
-    pred = np.where(Mte.astype(bool), pred, np.inf)
-    learned = pred.argmin(axis=1)
-    rule = []
+    # choices on the held-out queries, made by the library's policies
+    for idx in indexes.values():
+        thr.set_selector(idx, sel)
+    learned, rule = [], []
     for name, lr, ids, T, f, times in test:
-        rule.append(int(thr.select_variants(indexes[(name, lr)], [(ids, T)],
-                                            thr.THR_POLICY_RULE)[0]))
-    rule = np.array(rule)
+        ix = indexes[(name, lr)]
+        learned.append(int(thr.select_variants(ix, [(ids, T)], thr.THR_POLICY_LEARNED)[0]))
+        rule.append(int(thr.select_variants(ix, [(ids, T)], thr.THR_POLICY_RULE)[0]))
+    learned, rule = np.array(learned), np.array(rule)
     Tinf = np.where(Mte.astype(bool), Tte, np.inf)
     best = Tinf.argmin(axis=1)
     fixed = np.zeros(len(test), dtype=int)
@@ -267,7 +267,7 @@ def main():
     with open(os.path.join(args.out, "selector_eval.json"), "w") as f:
         json.dump(res, f, indent=1)
     np.savez_compressed(os.path.join(args.out, "selector_heldout.npz"), X=Xte, times=Tte,
-                        mask=Mte, rule=rule)
+                        mask=Mte, rule=rule, learned=learned)
     for idx in indexes.values():
         idx.close()
 

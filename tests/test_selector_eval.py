@@ -30,7 +30,13 @@ def test_learned_choice_beats_the_rule_on_held_out_queries():
     d, w = _load()
     X, times, mask, rule = d["X"], d["times"], d["mask"].astype(bool), d["rule"]
     y, _ = mlp.forward(np.asarray(w["params"], np.float32), X, w["mean"], w["istd"], bf16=True)
-    learned = np.where(mask, y, np.inf).argmin(axis=1)
+    # the learned policy: the fastest predicted variant, but another than the
+    # default (0) only when predicted at least 10% faster
+    yy = np.where(mask, y, np.inf)
+    yy[:, 0] -= np.log(1.1)
+    learned = yy.argmin(axis=1)
+    if "learned" in d:  # the library's own choices on the same queries
+        assert np.mean(learned == d["learned"]) > 0.99
     t = np.where(mask, times, np.inf)
     best = t.argmin(axis=1)
     rows = np.arange(len(t))
