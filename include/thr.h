@@ -82,10 +82,16 @@ typedef enum {
  *                          follows their literals: for sparse inputs
  *   THR_VARIANT_SCANCOUNT  ScanCount: one byte counter per row in shared
  *                          memory per subtile (Sec. 5.1), for very sparse
- *                          inputs; used when n <= 255, else CSA runs */
+ *                          inputs; used when n <= 255, else CSA runs
+ *   THR_VARIANT_SPLIT      THR_VARIANT_CSA with each subtile's inputs split
+ *                          among the four warps of a CTA, whose counters are
+ *                          then added: more parallelism for queries with
+ *                          few subtiles (small r) and many inputs; used when
+ *                          the counters need at most 8 bits, else CSA runs */
 #define THR_VARIANT_CSA 0x000u
 #define THR_VARIANT_SCANCOUNT 0x200u
 #define THR_VARIANT_POSITION 0x400u
+#define THR_VARIANT_SPLIT 0x600u
 #define THR_VARIANT_MASK 0xE00u
 
 /*
@@ -278,23 +284,25 @@ thr_status thr_autotune(const thr_index *idx, uint32_t nq, const uint32_t *id_of
  * Learned cost model of the variant selector (THR_POLICY_LEARNED).  The
  * paper predicts each algorithm's time with a fitted model and runs the one
  * predicted fastest (Sec. 8.1-8.2); here a multilayer perceptron
- * 16 -> 64 -> 64 -> 3 with ReLU predicts log(pass-A time) of the three
+ * 16 -> 64 -> 64 -> 4 with ReLU predicts log(pass-A time) of the four
  * counting variants (0 THR_VARIANT_CSA, 1 THR_VARIANT_POSITION,
- * 2 THR_VARIANT_SCANCOUNT) from the 16 features of thr_query_features,
+ * 2 THR_VARIANT_SCANCOUNT, 3 THR_VARIANT_SPLIT) from the 16 features of
+ * thr_query_features,
  * normalised as (x - mean) * istd.  Weights are BF16 (FP32 with
  * THR_SEL_FP32) and every sum is accumulated in FP32; training is minibatch
  * Adam on the mean squared error over the (row, variant) pairs whose mask
- * byte is non-zero.  The forward, backward and update steps are CUDA kernels
+ * byte is non-zero.  The learned policy runs the variant predicted fastest,
+ * but leaves THR_VARIANT_CSA only for a predicted gain of at least 10%.  The forward, backward and update steps are CUDA kernels
  * of this library, on the device current at creation.
  * Parameters (THR_SEL_PARAMS floats): W1[16][64] b1[64] W2[64][64] b2[64]
- * W3[64][3] b3[3], y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3.
- * X: rows x 16 floats, T (targets) and Y: rows x 3 floats, M: rows x 3
+ * W3[64][4] b3[4], y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3.
+ * X: rows x 16 floats, T (targets) and Y: rows x 4 floats, M: rows x 4
  * bytes; all host arrays.
  */
 typedef struct thr_selector thr_selector;
 #define THR_SEL_FEATURES 16
-#define THR_SEL_VARIANTS 3
-#define THR_SEL_PARAMS 5443
+#define THR_SEL_VARIANTS 4
+#define THR_SEL_PARAMS 5508
 #define THR_SEL_FP32 0x1u
 thr_status thr_selector_create(uint64_t seed, uint32_t flags, thr_selector **out);
 void thr_selector_free(thr_selector *sel);
@@ -322,7 +330,8 @@ thr_status thr_index_set_selector(thr_index *idx, const thr_selector *sel);
 
 /*
  * The counting variant (0 THR_VARIANT_CSA, 1 THR_VARIANT_POSITION,
- * 2 THR_VARIANT_SCANCOUNT) each query of a batch runs with under the policy
+ * 2 THR_VARIANT_SCANCOUNT, 3 THR_VARIANT_SPLIT) each query of a batch runs
+ * with under the policy
  * in flags (arguments as for thr_query_batch); nothing is run.
  */
 thr_status thr_select_variants(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
@@ -336,9 +345,10 @@ thr_status thr_select_variants(const thr_index *idx, uint32_t nq, const uint32_t
  *   THR_VARIANT_CSA        c[0] + c[1] * words + c[2] * words * S
  *   THR_VARIANT_POSITION   c[3] + c[4] * words + c[5] * words * S1
  *   THR_VARIANT_SCANCOUNT  c[6] + c[7] * words + c[8] * set bits
+ *   THR_VARIANT_SPLIT      c[9] + c[10] * words + c[11] * words * S
  * (words: compressed words of the inputs; S: counter bits of the grouped
  * kernel, S1: counter bits counting ones; set bits: of the inputs), refit
- * by least squares on measured times.  set (9 values) is applied when
+ * by least squares on measured times.  set (12 values) is applied when
  * non-NULL, then the current values go to get when non-NULL.
  */
 thr_status thr_rule_model(const double *set, double *get);

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE, like the rest of ``oracle/``: only tests, smoke() and
 the benchmark's CPU legs use it; the library does not import it.
 
-The network maps 16 features to 3 outputs, 16 -> 64 -> 64 -> 3 with ReLU on
+The network maps 16 features to V outputs (one per counting variant; V is
+given by the parameter count), 16 -> 64 -> 64 -> V with ReLU on
 the two hidden layers:  h1 = relu(W1^T x + b1), h2 = relu(W2^T h1 + b2),
 y = W3^T h2 + b3, with x = (features - mean) * istd.  The loss is the mean
 of (y - t)^2 over the (row, output) pairs whose mask is set.  Gradients are
@@ -13,7 +14,7 @@ when ``bf16`` is true, else the parameters themselves.  The paper's own
 selector is a linear time model per algorithm (Sec. 8.1); this network plays
 that role.
 
-Flat parameter layout: W1[16][64] b1[64] W2[64][64] b2[64] W3[64][3] b3[3].
+Flat parameter layout: W1[16][64] b1[64] W2[64][64] b2[64] W3[64][V] b3[V].
 
 Parity status: pinned by tests/test_oracle_mlp.py (central finite
 differences, the linear closed form when every unit is active, and bfloat16
@@ -23,10 +24,26 @@ from __future__ import annotations
 
 import numpy as np
 
-F, H, V = 16, 64, 3
-SHAPES = (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, V)),
-          ("b3", (V,)))
-NPARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+F, H, V = 16, 64, 4
+
+
+def shapes(v: int = V):
+    return (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, v)),
+            ("b3", (v,)))
+
+
+def nparams(v: int = V) -> int:
+    return sum(int(np.prod(s)) for _, s in shapes(v))
+
+
+NPARAMS = nparams()
+
+
+def outputs_of(size: int) -> int:
+    """V of a flat parameter vector of the given size."""
+    v = (size - nparams(0)) // (H + 1)
+    assert nparams(v) == size, size
+    return v
 
 
 def bf16_round(x) -> np.ndarray:
@@ -42,9 +59,8 @@ def bf16_round(x) -> np.ndarray:
 
 def unpack(params) -> dict:
     p = np.asarray(params, dtype=np.float64)
-    assert p.size == NPARAMS
     out, at = {}, 0
-    for name, shape in SHAPES:
+    for name, shape in shapes(outputs_of(p.size)):
         n = int(np.prod(shape))
         out[name] = p[at:at + n].reshape(shape)
         at += n

@@ -27,6 +27,7 @@ THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
 THR_NO_GRAPH = 0x1000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
+THR_VARIANT_SPLIT = 0x600
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",
@@ -384,9 +385,10 @@ def encode_many(word_arrays, r: int):
 
 # ------------------------------------------------------------------ selector
 
-SEL_FEATURES, SEL_VARIANTS, SEL_PARAMS = 16, 3, 5443
+SEL_FEATURES, SEL_VARIANTS, SEL_PARAMS = 16, 4, 5508
 THR_SEL_FP32 = 0x1
-VARIANT_FLAGS = (THR_VARIANT_CSA, THR_VARIANT_POSITION, THR_VARIANT_SCANCOUNT)
+VARIANT_FLAGS = (THR_VARIANT_CSA, THR_VARIANT_POSITION, THR_VARIANT_SCANCOUNT,
+                 THR_VARIANT_SPLIT)
 
 
 def _f32(a) -> np.ndarray:
@@ -500,12 +502,12 @@ def select_variants(idx: Index, queries, flags: int) -> np.ndarray:
 
 
 def rule_model(coeffs=None) -> np.ndarray:
-    """Get (and with coeffs, first set) the rule chooser's 9 coefficients."""
-    get = np.zeros(9, np.float64)
+    """Get (and with coeffs, first set) the rule chooser's 12 coefficients."""
+    get = np.zeros(12, np.float64)
     setp = None
     if coeffs is not None:
         setp = np.ascontiguousarray(coeffs, dtype=np.float64)
-        assert setp.size == 9
+        assert setp.size == 12
     _check(load().thr_rule_model(ctypes.c_void_p(setp.ctypes.data if setp is not None else 0),
                                  ctypes.c_void_p(get.ctypes.data)), "thr_rule_model")
     return get

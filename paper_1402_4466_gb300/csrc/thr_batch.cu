@@ -177,7 +177,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         // the chunk's shape and its launch configuration
         uint32_t present = 0;
         double sum_n = 0;
-        int widest[3] = {-1, -1, -1};  // per family
+        int widest[4] = {-1, -1, -1, -1};  // per family
         for (uint32_t s = 0; s < Q; ++s) {
             const int c = qcls[q0 + s];
             present |= 1u << c;
@@ -219,8 +219,10 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
             const uint64_t items = uint64_t(cnt) * NG;
             double ctas = double(per_sm[c]) * idx->num_sms;
             if ((cfg & kTuneSplit) && work_all > 0) ctas *= work[c] / work_all;
+            // a CTA takes kNW items at a time, or one with the inputs split
+            const uint64_t per_cta = class_family(c) == 3 ? 1 : kNW;
             L.grid = int(std::max<uint64_t>(
-                1, std::min<uint64_t>((items + kNW - 1) / kNW, uint64_t(ctas + 0.5))));
+                1, std::min<uint64_t>((items + per_cta - 1) / per_cta, uint64_t(ctas + 0.5))));
             launches.push_back(L);
             key = fnv(key, uint64_t(c) << 8 | 1);
         }

@@ -76,7 +76,7 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
                           bool* used);
 uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint32_t T);
 int variant_of_flag(uint32_t variant_flag);
-constexpr int kRuleCoeffs = 9;
+constexpr int kRuleCoeffs = 12;
 void set_rule_model(const double* c);
 void get_rule_model(double* c);
 

@@ -124,27 +124,27 @@ thr_status report_error(thr_status st, const char* msg) { return fail(st, "%s", 
 const KernelEntry* kernel_table(int* count) {
     static const KernelEntry tab[] = {
         {1, launch_threshold_1, occupancy_threshold_1, launch_threshold_pos_1,
-         occupancy_threshold_pos_1},
+         occupancy_threshold_pos_1, launch_split_1, occupancy_split_1},
         {2, launch_threshold_2, occupancy_threshold_2, launch_threshold_pos_2,
-         occupancy_threshold_pos_2},
+         occupancy_threshold_pos_2, launch_split_2, occupancy_split_2},
         {3, launch_threshold_3, occupancy_threshold_3, launch_threshold_pos_3,
-         occupancy_threshold_pos_3},
+         occupancy_threshold_pos_3, launch_split_3, occupancy_split_3},
         {4, launch_threshold_4, occupancy_threshold_4, launch_threshold_pos_4,
-         occupancy_threshold_pos_4},
+         occupancy_threshold_pos_4, launch_split_4, occupancy_split_4},
         {5, launch_threshold_5, occupancy_threshold_5, launch_threshold_pos_5,
-         occupancy_threshold_pos_5},
+         occupancy_threshold_pos_5, launch_split_5, occupancy_split_5},
         {6, launch_threshold_6, occupancy_threshold_6, launch_threshold_pos_6,
-         occupancy_threshold_pos_6},
+         occupancy_threshold_pos_6, launch_split_6, occupancy_split_6},
         {7, launch_threshold_7, occupancy_threshold_7, launch_threshold_pos_7,
-         occupancy_threshold_pos_7},
+         occupancy_threshold_pos_7, launch_split_7, occupancy_split_7},
         {8, launch_threshold_8, occupancy_threshold_8, launch_threshold_pos_8,
-         occupancy_threshold_pos_8},
+         occupancy_threshold_pos_8, launch_split_8, occupancy_split_8},
         {10, launch_threshold_10, occupancy_threshold_10, launch_threshold_pos_10,
-         occupancy_threshold_pos_10},
+         occupancy_threshold_pos_10, nullptr, nullptr},
         {12, launch_threshold_12, occupancy_threshold_12, launch_threshold_pos_12,
-         occupancy_threshold_pos_12},
+         occupancy_threshold_pos_12, nullptr, nullptr},
         {16, launch_threshold_16, occupancy_threshold_16, launch_threshold_pos_16,
-         occupancy_threshold_pos_16},
+         occupancy_threshold_pos_16, nullptr, nullptr},
     };
     *count = int(sizeof tab / sizeof tab[0]);
     return tab;
@@ -487,7 +487,13 @@ thr_status thr_select_variants(const thr_index* idx, uint32_t nq, const uint32_t
     if (ps != THR_OK) return ps;
     for (uint32_t q = 0; q < nq; ++q) {
         const uint32_t n = id_off[q + 1] - id_off[q];
-        variant[q] = (var[q] == kVarScanCount && n > 255) ? uint8_t(kVarCsa) : var[q];
+        int cls = 0;
+        uint32_t z = 0;
+        resolve_variant(n, T[q], var[q], &cls, &z);
+        // the variant that actually runs (fallbacks of ScanCount and split)
+        const int fam = class_family(cls);
+        variant[q] = uint8_t(fam == 0 ? kVarCsa : fam == 1 ? kVarScanCount
+                                                : fam == 2 ? kVarPos : kVarSplit);
     }
     return THR_OK;
 }

@@ -210,6 +210,32 @@ struct Counters {
         if constexpr (S > 1) add1<1>(h, k1);
         else sticky[h] |= k1;
     }
+    // the counters of this lane to dst[(k * 8 + h) * 32 + lane] (slice k,
+    // half h; the sticky slice is k = S)
+    __device__ __forceinline__ void store(uint32_t* dst, uint32_t lane) const {
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) dst[(k * 8 + h) * 32 + lane] = c[k][h];
+            dst[(S * 8 + h) * 32 + lane] = sticky[h];
+        }
+    }
+    // add counters stored by store(): a ripple-carry adder per slice; the
+    // carry out of the top slice and the other sticky bit saturate
+    __device__ __forceinline__ void add_from(const uint32_t* src, uint32_t lane) {
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            uint32_t cy = 0;
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                const uint32_t b = src[(k * 8 + h) * 32 + lane];
+                const uint32_t a = c[k][h];
+                c[k][h] = lop3<kXor3>(a, b, cy);
+                cy = lop3<kMaj3>(a, b, cy);
+            }
+            sticky[h] = lop3<kOr3>(sticky[h], cy, src[(S * 8 + h) * 32 + lane]);
+        }
+    }
     // bit-sliced "count >= thr" (thr < 2^S), most significant slice first
     __device__ __forceinline__ uint32_t ge(int h, uint32_t thr) const {
         uint32_t eq = ~0u, gt = 0u;

@@ -26,7 +26,12 @@ cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t s
     const KernelEntry* tab = kernel_table(&cnt);
     const int w = class_width(cls);
     if (cls < 0 || cls >= kNumClasses || w >= cnt) return cudaErrorInvalidValue;
-    return class_family(cls) == 2 ? tab[w].launch_pos(p, grid, st) : tab[w].launch(p, grid, st);
+    switch (class_family(cls)) {
+        case 2: return tab[w].launch_pos(p, grid, st);
+        case 3: return tab[w].launch_split ? tab[w].launch_split(p, grid, st)
+                                           : cudaErrorInvalidValue;
+        default: return tab[w].launch(p, grid, st);
+    }
 }
 
 }  // namespace
@@ -85,6 +90,10 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
         return;
     }
     choose_class(n, T, cls, zmode);
+    if (v == kVarSplit) {
+        if (*cls < kSplitWidths) *cls += kClassSplit;
+        return;
+    }
     if (v == kVarPos) {  // ones counting: the first width with 2^S > T
         int cnt = 0;
         const KernelEntry* tab = kernel_table(&cnt);
@@ -106,7 +115,12 @@ cudaError_t class_occupancy(int cls, int* per_sm) {
     const KernelEntry* tab = kernel_table(&cnt);
     const int w = class_width(cls);
     if (cls < 0 || cls >= kNumClasses || w >= cnt) return cudaErrorInvalidValue;
-    return class_family(cls) == 2 ? tab[w].occupancy_pos(per_sm) : tab[w].occupancy(per_sm);
+    switch (class_family(cls)) {
+        case 2: return tab[w].occupancy_pos(per_sm);
+        case 3: return tab[w].occupancy_split ? tab[w].occupancy_split(per_sm)
+                                              : cudaErrorInvalidValue;
+        default: return tab[w].occupancy(per_sm);
+    }
 }
 
 cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,

@@ -16,16 +16,24 @@ namespace thr {
 // Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
 // kernel_table()[c].S (grouped decode), kClassScanCount the ScanCount
 // kernel, kClassPos + c carry-save of width kernel_table()[c].S with the
-// position-major decode of mixed inputs.
+// position-major decode of mixed inputs, kClassSplit + c carry-save with
+// the inputs split among the CTA's warps (widths up to kSplitWidths).
 constexpr int kNumWidths = 11;
+constexpr int kSplitWidths = 8;  // S = 1..8
 constexpr int kClassScanCount = kNumWidths;
 constexpr int kClassPos = kNumWidths + 1;
-constexpr int kNumClasses = 2 * kNumWidths + 1;
+constexpr int kClassSplit = 2 * kNumWidths + 1;
+constexpr int kNumClasses = kClassSplit + kSplitWidths;
 static_assert(kNumClasses <= 32, "class sets are 32-bit masks");
-// Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major.
-inline int class_family(int c) { return c < kNumWidths ? 0 : (c == kClassScanCount ? 1 : 2); }
+// Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major,
+// 3 split inputs.
+inline int class_family(int c) {
+    return c < kNumWidths ? 0 : (c == kClassScanCount ? 1 : (c < kClassSplit ? 2 : 3));
+}
 // Counter-width index of a carry-save class.
-inline int class_width(int c) { return c < kNumWidths ? c : c - kClassPos; }
+inline int class_width(int c) {
+    return c < kNumWidths ? c : (c < kClassSplit ? c - kClassPos : c - kClassSplit);
+}
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
 // chunk, work items in `order` (0 query-major, 1 subtile-major), `grid` CTAs.
@@ -88,8 +96,10 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
 //   kVarPos        carry-save bit slices counting ones; mixed inputs decoded
 //                  position-major (cost follows their literals)
 //   kVarScanCount  ScanCount byte counters (n <= 255; else kVarCsa runs)
-constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2;
-constexpr int kNumVariants = 3;
+//   kVarSplit      grouped carry-save with each subtile's inputs split among
+//                  the four warps of a CTA (S <= 8; else kVarCsa runs)
+constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2, kVarSplit = 3;
+constexpr int kNumVariants = 4;
 // Kernel class and zero counting of a query run with variant v.
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 

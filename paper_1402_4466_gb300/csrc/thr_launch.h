@@ -17,6 +17,8 @@ struct KernelEntry {
     OccupancyFn occupancy;
     LaunchFn launch_pos;      // position-major decode of mixed inputs
     OccupancyFn occupancy_pos;
+    LaunchFn launch_split;    // inputs split among the CTA's warps (S <= 8), or null
+    OccupancyFn occupancy_split;
 };
 
 // Pass A with ScanCount counters (thr_scancount.cu): n <= 255, ones only.
@@ -32,6 +34,19 @@ const KernelEntry* kernel_table(int* count);
     cudaError_t occupancy_threshold_##S(int*);                                   \
     cudaError_t launch_threshold_pos_##S(const PassAParams&, int, cudaStream_t); \
     cudaError_t occupancy_threshold_pos_##S(int*);
+
+#define THR_DECLARE_SPLIT(S)                                                \
+    cudaError_t launch_split_##S(const PassAParams&, int, cudaStream_t);     \
+    cudaError_t occupancy_split_##S(int*);
+
+THR_DECLARE_SPLIT(1)
+THR_DECLARE_SPLIT(2)
+THR_DECLARE_SPLIT(3)
+THR_DECLARE_SPLIT(4)
+THR_DECLARE_SPLIT(5)
+THR_DECLARE_SPLIT(6)
+THR_DECLARE_SPLIT(7)
+THR_DECLARE_SPLIT(8)
 
 THR_DECLARE_WIDTH(1)
 THR_DECLARE_WIDTH(2)

@@ -14,7 +14,7 @@ namespace thr {
 
 constexpr int kSelFeatures = 16;
 constexpr int kSelHidden = 64;
-constexpr int kSelVariants = 3;
+constexpr int kSelVariants = 4;
 constexpr int kSelParams = kSelFeatures * kSelHidden + kSelHidden + kSelHidden * kSelHidden +
                            kSelHidden + kSelHidden * kSelVariants + kSelVariants;
 

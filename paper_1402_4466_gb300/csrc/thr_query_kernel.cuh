@@ -246,20 +246,23 @@ struct CsaCount {
 // policy (carry-save bit slices, or ScanCount counters).  kPos: mixed inputs
 // go through the position-major decode (ones counting; the host never sets
 // zmode for these kernels), literal runs through the grouped one.
-template <class Count, bool kPos = false>
-__device__ __forceinline__ void subtile_result(const PassAParams& p, const QView& q,
-                                               uint32_t x0, uint32_t x1, uint32_t lane,
-                                               WarpSmem& ws, Count& count,
-                                               uint64_t (&o)[kRows]) {
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) o[q] = 0;
-    if (x0 >= p.W) return;
+// Counting part of subtile_result: classify the query's inputs over the
+// subtile, count k (ones fills) and d (inputs with literals) and add the
+// active inputs into `count`.  kPart: the inputs are one part of a query
+// whose other parts other warps count, so the totals are not known and the
+// subtile is never pruned here.
+template <class Count, bool kPos = false, bool kPart = false>
+__device__ __forceinline__ void count_subtile(const PassAParams& p, const QView& q,
+                                              uint32_t x0, uint32_t x1, uint32_t lane,
+                                              WarpSmem& ws, Count& count, uint32_t& k_ones,
+                                              uint32_t& d_act) {
     const uint32_t g = x0 / kGW;
     count.begin();
-    uint32_t k_ones = 0, d_act = 0;
+    k_ones = 0;
+    d_act = 0;
     const bool one_chunk = q.n() <= uint32_t(kCH);
     bool pruned = false;
-    if (!one_chunk) {  // classify every input first so that pruning still applies
+    if (!one_chunk && !kPart) {  // classify every input first so that pruning still applies
         for (uint32_t i0 = 0; i0 < q.n(); i0 += 32) {
             const uint32_t i = i0 + lane;
             uint32_t cls = 0;
@@ -295,7 +298,7 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
                     }
                 }
             }
-            if (one_chunk) k_ones += __popc(__ballot_sync(~0u, cls == 1));
+            if (one_chunk || kPart) k_ones += __popc(__ballot_sync(~0u, cls == 1));
             if constexpr (kPos) {  // literal runs from the front, mixed from the back
                 const uint32_t a2 = __ballot_sync(~0u, cls == 2);
                 const uint32_t a3 = __ballot_sync(~0u, cls == 3);
@@ -315,7 +318,9 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
         if (one_chunk) {  // run-aware pruning (Sec. 6.4 cases 1 and 2)
             d_act = nrec;
             const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
-            if (Tp <= 0 || Tp > int64_t(d_act)) break;
+            if (!kPart && (Tp <= 0 || Tp > int64_t(d_act))) break;
+        } else if (kPart) {
+            d_act += nrec;
         }
         if constexpr (kPos) {
             // 2'. literal runs a group at a time, mixed inputs position-major
@@ -349,14 +354,24 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
         }
         __syncwarp();
     }
-    // 3. compare with T' = T - k (or the zeros with d - T' + 1)
-    const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
+}
+
+// Compare with T' = T - k (or count the zeros against d - T' + 1) and mask
+// the words past W: the subtile's result words (row r of the lane in o[r]).
+template <class Count>
+__device__ __forceinline__ void finish_subtile(const PassAParams& p, uint32_t T, uint32_t zmode,
+                                               uint32_t k_ones, uint32_t d_act, uint32_t x0,
+                                               uint32_t lane, Count& count,
+                                               uint64_t (&o)[kRows]) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) o[r] = 0;
+    const int64_t Tp = int64_t(T) - int64_t(k_ones);
     if (Tp <= 0) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) o[r] = ~0ull;
     } else if (Tp <= int64_t(d_act)) {
-        const uint32_t thr = q.zmode() ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
-        count.finish(thr, q.zmode() ? ~0u : 0u, o);
+        const uint32_t thr = zmode ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
+        count.finish(thr, zmode ? ~0u : 0u, o);
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -364,6 +379,16 @@ __device__ __forceinline__ void subtile_result(const PassAParams& p, const QView
         if (x >= p.W) o[r] = 0;
         else if (x == p.W - 1 && p.ragged) o[r] &= (1ull << p.ragged) - 1;
     }
+}
+
+template <class Count, bool kPos = false>
+__device__ __forceinline__ void subtile_result(const PassAParams& p, const QView& q,
+                                               uint32_t x0, uint32_t x1, uint32_t lane,
+                                               WarpSmem& ws, Count& count,
+                                               uint64_t (&o)[kRows]) {
+    uint32_t k_ones = 0, d_act = 0;
+    count_subtile<Count, kPos, false>(p, q, x0, x1, lane, ws, count, k_ones, d_act);
+    finish_subtile(p, q.T(), q.zmode(), k_ones, d_act, x0, lane, count, o);
 }
 
 // Canonical re-encoding, part 1 (per subtile, by its warp).  o[q] is word
@@ -453,6 +478,51 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
     return L;
 }
 
+// The warp's view of a query (or of a part of its inputs): n ids from
+// ids_off, its threshold and counting mode; ids and stream offsets are
+// cached in the warp's shared memory when n <= kCH.
+__device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, uint32_t ids_off,
+                                           uint32_t n, uint32_t T, uint32_t zmode,
+                                           uint32_t lane) {
+    __syncwarp();
+    if (lane == 0) {
+        ws.qn = n;
+        ws.qT = T;
+        ws.qz = zmode;
+        ws.qoff = ids_off;
+    }
+    if (n <= uint32_t(kCH)) {
+        for (uint32_t i = lane; i < n; i += 32) {
+            const uint32_t b = __ldg(p.ids + ids_off + i);
+            ws.ids[i] = b;
+            ws.woff[i] = p.desc[b].woff;
+        }
+    }
+    __syncwarp();
+}
+
+// Re-encoding part 1 of a finished subtile: rows -> 4 consecutive words per
+// lane, local scan, the result words (unless one fill class) and the
+// aggregate to the slot's scratch.
+__device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws, uint32_t slot,
+                                              uint32_t g, uint32_t x0, uint32_t x1,
+                                              uint32_t lane, const uint64_t (&orow)[kRows]) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
+    __syncwarp();
+    uint64_t o[kWPL];
+#pragma unroll
+    for (int k = 0; k < kWPL; ++k) o[k] = ws.tw[kWPL * lane + k];
+    __syncwarp();
+    const LocalScan L = local_scan(x0, x1, lane, o);
+    const uint64_t sg = uint64_t(slot) * p.NG + g;
+    if (L.A.nh || L.A.nl) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) p.U[sg * kGW + 32 * r + lane] = orow[r];
+    }
+    if (lane == 0) agg_store_plain(p.aggs + sg * kAggWords, L.A);
+}
+
 // Pass A driver: each warp of the persistent grid takes every (grid
 // warps)-th work item of the launch, or with a work counter the next free
 // one, an item being one (query, subtile) pair: query-major
@@ -492,42 +562,14 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
         const uint32_t s = __ldg(p.list + li);
         if (s != cur) {  // a new query: its parameters, and its ids when they fit
             const QDesc d = p.qd[s];
-            __syncwarp();
-            if (lane == 0) {
-                ws.qn = d.n;
-                ws.qT = d.T;
-                ws.qz = d.zmode;
-                ws.qoff = d.ids_off;
-            }
-            if (d.n <= uint32_t(kCH)) {
-                for (uint32_t i = lane; i < d.n; i += 32) {
-                    const uint32_t b = __ldg(p.ids + d.ids_off + i);
-                    ws.ids[i] = b;
-                    ws.woff[i] = p.desc[b].woff;
-                }
-            }
-            __syncwarp();
+            load_query(p, ws, d.ids_off, d.n, d.T, d.zmode, lane);
             cur = s;
         }
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint64_t orow[kRows];
         subtile_result<Count, kPos>(p, q, x0, x1, lane, ws, count, orow);
-        // rows -> 4 consecutive words per lane (the scan's order)
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
-        __syncwarp();
-        uint64_t o[kWPL];
-#pragma unroll
-        for (int k = 0; k < kWPL; ++k) o[k] = ws.tw[kWPL * lane + k];
-        __syncwarp();
-        const LocalScan L = local_scan(x0, x1, lane, o);
-        const uint64_t sg = uint64_t(cur) * p.NG + g;
-        if (L.A.nh || L.A.nl) {
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) p.U[sg * kGW + 32 * r + lane] = orow[r];
-        }
-        if (lane == 0) agg_store_plain(p.aggs + sg * kAggWords, L.A);
+        store_subtile(p, ws, cur, g, x0, x1, lane, orow);
         it = p.work ? __shfl_sync(~0u, next, 0) : it + nwarps;
     }
 }
@@ -543,6 +585,79 @@ __global__ void __launch_bounds__(kNT, (S <= 3 ? 6 : (S <= 6 ? 4 : 2))) k_thresh
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     CsaCount<S> count;
     pass_a<CsaCount<S>, kPos>(p, sm, count);
+}
+
+// Pass A with the inputs of every subtile split among the CTA's warps: the
+// CTA takes one (query, subtile) item at a time, warp w counts the w-th
+// quarter of the query's inputs into its own carry-save counters, and warp 0
+// adds the other warps' counter slices (a ripple adder per slice, the sticky
+// bits ORed), compares and re-encodes.  Four warps work on one subtile, so
+// a query with few subtiles and many inputs finishes in about a quarter of
+// the time one warp per subtile needs; with many subtiles the extra
+// exchange only costs.  Counter words of warps 1-3 pass through dynamic
+// shared memory after CtaSmem.
+template <int S>
+__global__ void __launch_bounds__(kNT, 4) k_threshold_split(const PassAParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
+    uint32_t* part = reinterpret_cast<uint32_t*>(smem_raw + sizeof(CtaSmem));
+    __shared__ uint32_t kd[kNW][2];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem& ws = sm.w[wid];
+    const QView q{ws, p.ids};
+    CsaCount<S> count;
+    constexpr uint32_t kSliceWords = (S + 1) * 8 * 32;  // one warp's counters
+    const uint32_t nitems = p.nlist * p.NG;
+    uint32_t cur = ~0u;
+    uint32_t T = 0, zmode = 0;
+    for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const uint32_t li = it / p.NG, g = it - li * p.NG;
+        const uint32_t s = __ldg(p.list + li);
+        if (s != cur) {  // this warp's share of the new query's inputs
+            const QDesc d = p.qd[s];
+            const uint32_t a = uint32_t(uint64_t(d.n) * wid / kNW);
+            const uint32_t b = uint32_t(uint64_t(d.n) * (wid + 1) / kNW);
+            load_query(p, ws, d.ids_off + a, b - a, d.T, d.zmode, lane);
+            T = d.T;
+            zmode = d.zmode;
+            cur = s;
+        }
+        const uint32_t x0 = g * uint32_t(kGW);
+        const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
+        uint32_t k = 0, dd = 0;
+        if (q.n() > 0)
+            count_subtile<CsaCount<S>, false, true>(p, q, x0, x1, lane, ws, count, k, dd);
+        else
+            count.begin();
+        if (lane == 0) {
+            kd[wid][0] = k;
+            kd[wid][1] = dd;
+        }
+        __syncthreads();
+        uint32_t K = 0, D = 0;
+#pragma unroll
+        for (int w = 0; w < kNW; ++w) {
+            K += kd[w][0];
+            D += kd[w][1];
+        }
+        const int64_t Tp = int64_t(T) - int64_t(K);
+        const bool live = Tp > 0 && Tp <= int64_t(D);
+        if (live && wid > 0) count.cnt.store(part + (wid - 1) * kSliceWords, lane);
+        __syncthreads();
+        if (wid == 0) {
+            if (live)
+                for (int w = 1; w < kNW; ++w) count.cnt.add_from(part + (w - 1) * kSliceWords, lane);
+            uint64_t orow[kRows];
+            finish_subtile(p, T, zmode, K, D, x0, lane, count, orow);
+            store_subtile(p, ws, cur, g, x0, x1, lane, orow);
+        }
+        __syncthreads();
+    }
+}
+
+template <int S>
+constexpr size_t split_smem_bytes() {
+    return sizeof(CtaSmem) + (kNW - 1) * (S + 1) * 8 * 32 * sizeof(uint32_t);
 }
 
 }  // namespace thr

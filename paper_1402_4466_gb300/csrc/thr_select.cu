@@ -25,6 +25,7 @@ namespace {
 //   carry-save, grouped   a0 + a1 * words + a2 * words * S
 //   carry-save, position  c0 + c1 * words + c2 * words * S1
 //   ScanCount             b0 + b1 * words + b2 * set bits
+//   carry-save, split     s0 + s1 * words + s2 * words * S
 // words = compressed words of the query's inputs, S = counter bits of the
 // grouped kernel (the smaller of the ones and zeros counts), S1 = counter
 // bits when counting ones.  The defaults are placeholders until
@@ -33,6 +34,7 @@ struct RuleModel {
     double a0 = 0, a1 = 1.0, a2 = 0.25;
     double c0 = 0, c1 = 1.0, c2 = 0.3;
     double b0 = 0, b1 = 1.0, b2 = 0.35;
+    double s0 = 0, s1 = 1.0, s2 = 0.3;
 };
 std::mutex g_rule_mu;
 RuleModel g_rule;
@@ -50,13 +52,14 @@ int bitlen(uint64_t v) {
 
 void set_rule_model(const double* c) {
     std::lock_guard<std::mutex> lk(g_rule_mu);
-    g_rule = RuleModel{c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8]};
+    g_rule = RuleModel{c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9], c[10], c[11]};
 }
 
 void get_rule_model(double* c) {
     std::lock_guard<std::mutex> lk(g_rule_mu);
     const RuleModel& m = g_rule;
-    const double v[kRuleCoeffs] = {m.a0, m.a1, m.a2, m.c0, m.c1, m.c2, m.b0, m.b1, m.b2};
+    const double v[kRuleCoeffs] = {m.a0, m.a1, m.a2, m.c0, m.c1, m.c2,
+                                   m.b0, m.b1, m.b2, m.s0, m.s1, m.s2};
     for (int i = 0; i < kRuleCoeffs; ++i) c[i] = v[i];
 }
 
@@ -74,12 +77,14 @@ uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
     const bool counted = T >= 1 && T <= n;
     const double S1 = counted ? double(bitlen(T)) : 1.0;
     const double S = counted ? double(std::min(bitlen(T), bitlen(uint64_t(n) - T + 1))) : 1.0;
-    const double t[3] = {m.a0 + m.a1 * words + m.a2 * words * S,
+    const double t[4] = {m.a0 + m.a1 * words + m.a2 * words * S,
                          m.c0 + m.c1 * words + m.c2 * words * S1,
-                         m.b0 + m.b1 * words + m.b2 * bits};
+                         m.b0 + m.b1 * words + m.b2 * bits,
+                         m.s0 + m.s1 * words + m.s2 * words * S};
     int best = kVarCsa;
-    for (int v = 1; v < 3; ++v) {
+    for (int v = 1; v < 4; ++v) {
         if (v == kVarScanCount && n > 255) continue;
+        if (v == kVarSplit && S > 8) continue;
         if (t[v] < t[best]) best = v;
     }
     return uint8_t(best);
@@ -90,6 +95,7 @@ int variant_of_flag(uint32_t f) {
         case THR_VARIANT_CSA: return kVarCsa;
         case THR_VARIANT_POSITION: return kVarPos;
         case THR_VARIANT_SCANCOUNT: return kVarScanCount;
+        case THR_VARIANT_SPLIT: return kVarSplit;
         default: return -1;
     }
 }
@@ -147,6 +153,14 @@ void query_features(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
 
 constexpr float kSwitchGain = 0.10f;
 
+// The split kernel exists for counter widths up to 8 bits.
+bool split_applies(uint32_t n, uint32_t T) {
+    int cls = 0;
+    uint32_t z = 0;
+    choose_class(n, T, &cls, &z);
+    return cls < kSplitWidths;
+}
+
 // With a cost model attached to the index: features of every query, one
 // forward pass for the batch, and per query the variant with the smallest
 // predicted time among those it can run (ScanCount needs n <= 255).
@@ -177,6 +191,7 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
         float best_y = y[kVarCsa] - margin;
         for (int v = 0; v < kSelVariants; ++v) {
             if (v == kVarCsa || (v == kVarScanCount && n > 255)) continue;
+            if (v == kVarSplit && !split_applies(n, T[q])) continue;
             if (y[v] < best_y) {
                 best = v;
                 best_y = y[v];

@@ -20,7 +20,12 @@ PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weight
 
 def load(path: str = PATH) -> dict:
     with open(path) as f:
-        return json.load(f)
+        d = json.load(f)
+    if len(d["params"]) != thr.SEL_PARAMS or len(d.get("rule_coefficients", [])) not in (0, 12):
+        raise ValueError(f"{path}: written for another library version "
+                         f"({len(d['params'])} parameters, {thr.SEL_PARAMS} expected); "
+                         "retrain with train_selector")
+    return d
 
 
 def make_selector(path: str = PATH) -> "thr.Selector":

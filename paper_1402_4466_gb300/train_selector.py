@@ -41,7 +41,7 @@ import synth  # noqa: E402
 import paper_1402_4466_gb300 as thr  # noqa: E402
 
 NB = 256
-VARIANTS = ("csa", "position", "scancount")
+VARIANTS = ("csa", "position", "scancount", "split")
 
 
 def _gen_plain(args):
@@ -87,11 +87,14 @@ def draw_query(rng, log_rs):
 def measure(idx, ids, T, reps, dout):
     """Minimum pass-A ms per variant (nan where a variant does not apply)
     and the result length."""
-    times = np.full(3, np.nan)
+    times = np.full(len(VARIANTS), np.nan)
     length = 0
     for v, vf in enumerate(thr.VARIANT_FLAGS):
         if v == 2 and len(ids) > 255:
             continue
+        if v == 3 and max(int(T).bit_length(), 1) > 8 and \
+                int(len(ids) - T + 1).bit_length() > 8:
+            continue  # no split kernel for counters wider than 8 bits
         best = math.inf
         for k in range(reps + 1):
             length = thr.thr_query(idx, ids, T, out=dout, flags=vf | thr.THR_PROFILE)
@@ -143,12 +146,12 @@ def idx_bits(idx):
 def fit_rule(rows, indexes):
     """Least squares fits, times in ms: t = a0 + a1 w + a2 w S (grouped
     carry-save), c0 + c1 w + c2 w S1 (position-major), b0 + b1 w + b2 bits
-    (ScanCount)."""
-    D = [([], []), ([], []), ([], [])]
+    (ScanCount), s0 + s1 w + s2 w S (split inputs)."""
+    D = [([], []), ([], []), ([], []), ([], [])]
     for name, lr, ids, T, f, times in rows:
         w, bits, S, S1 = rule_design(indexes[(name, lr)], ids, T)
-        xs = ([1.0, w, w * S], [1.0, w, w * S1], [1.0, w, bits])
-        for v in range(3):
+        xs = ([1.0, w, w * S], [1.0, w, w * S1], [1.0, w, bits], [1.0, w, w * S])
+        for v in range(4):
             if not math.isnan(times[v]):
                 D[v][0].append(xs[v])
                 D[v][1].append(times[v])
@@ -232,7 +235,7 @@ def main():
     best = Tinf.argmin(axis=1)
     fixed = np.zeros(len(test), dtype=int)
     single = int(np.argmin([np.sum(np.where(Mte[:, v].astype(bool), Tte[:, v], Tte[:, 0]))
-                            for v in range(3)]))
+                            for v in range(len(VARIANTS))]))
     single_choice = np.where(Mte[:, single].astype(bool), single, 0)
     res = {
         "queries": {"train": len(train), "held_out": len(test)},

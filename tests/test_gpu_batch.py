@@ -140,13 +140,15 @@ def test_batch_many_inputs_per_query(mixed):
           (rng.integers(0, 48, 200).astype(np.uint32), 1),
           (rng.integers(0, 48, 129).astype(np.uint32), 129),
           (rng.integers(0, 48, 260).astype(np.uint32), 30)]
-    for fl in (0, thr.THR_VARIANT_SCANCOUNT, thr.THR_VARIANT_POSITION, thr.THR_POLICY_RULE):
+    for fl in (0, thr.THR_VARIANT_SCANCOUNT, thr.THR_VARIANT_POSITION, thr.THR_VARIANT_SPLIT,
+               thr.THR_POLICY_RULE):
         off, ln, pool = thr.thr_query_batch(g, qs, flags=fl)
         _check(g, o, qs, off, ln, pool)
 
 
 @pytest.mark.parametrize("flags", [thr.THR_VARIANT_SCANCOUNT, thr.THR_VARIANT_POSITION,
-                                   thr.THR_POLICY_RULE, thr.THR_POLICY_LEARNED])
+                                   thr.THR_VARIANT_SPLIT, thr.THR_POLICY_RULE,
+                                   thr.THR_POLICY_LEARNED])
 def test_batch_policies(mixed, flags):
     g, o, r = mixed
     qs = _queries(9, 48, 30)

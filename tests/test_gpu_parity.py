@@ -268,3 +268,39 @@ def test_position_many_criteria_full_size(many_criteria_full):
     p = Pair(words, r)
     for T in (*synth.MANY_TS, 1, 64):
         p.check(list(range(synth.MANY_N)), T, POS)
+
+
+# ---- the split-input kernel (the CTA's warps share a subtile's inputs)
+
+SPLIT = thr.THR_VARIANT_SPLIT
+
+
+def test_split_random_tiny_all_thresholds():
+    rng = np.random.default_rng(404)
+    for _ in range(20):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 4096, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        for T in range(0, n + 2):
+            p.check(list(range(n)), T, SPLIT)
+
+
+def test_split_many_inputs_and_chunks():
+    """Fewer inputs than warps, and parts above one record chunk (n > 512)."""
+    r = (1 << 17) + 999
+    words, _ = synth.many_criteria(15, 40, r)
+    p = Pair(words, r)
+    for ids in ([3], [0, 7], [1, 2, 3], list(range(40))):
+        for T in sorted({0, 1, 2, len(ids), len(ids) + 1}):
+            p.check(ids, T, SPLIT)
+    rng = np.random.default_rng(16)
+    ids = rng.integers(0, 40, size=700).tolist()
+    for T in (1, 3, 100, 350, 690, 700):
+        p.check(ids, T, SPLIT)  # S > 8 for the middle thresholds: carry-save runs
+
+
+def test_split_many_criteria_full_size(many_criteria_full):
+    words, r = many_criteria_full
+    p = Pair(words, r)
+    for T in (*synth.MANY_TS, 1, 64):
+        p.check(list(range(synth.MANY_N)), T, SPLIT)

@@ -24,8 +24,8 @@ def cuda():
 def _data(seed, rows):
     rng = np.random.default_rng(seed)
     X = (rng.standard_normal((rows, 16)) * 3 + 5).astype(np.float32)
-    T = rng.standard_normal((rows, 3)).astype(np.float32)
-    M = (rng.random((rows, 3)) < 0.8).astype(np.uint8)
+    T = rng.standard_normal((rows, thr.SEL_VARIANTS)).astype(np.float32)
+    M = (rng.random((rows, thr.SEL_VARIANTS)) < 0.8).astype(np.uint8)
     mean = X.mean(axis=0).astype(np.float32)
     istd = (1.0 / X.std(axis=0)).astype(np.float32)
     return X, T, M, mean, istd
@@ -60,8 +60,8 @@ def test_training_lowers_the_loss():
     """A smooth target of the features: Adam on the CUDA passes fits it."""
     rng = np.random.default_rng(5)
     X = rng.standard_normal((4000, 16)).astype(np.float32)
-    w = rng.standard_normal((16, 3)).astype(np.float32) * 0.5
-    T = np.tanh(X @ w) + 0.3 * (X[:, :3] ** 2)
+    w = rng.standard_normal((16, thr.SEL_VARIANTS)).astype(np.float32) * 0.5
+    T = np.tanh(X @ w) + 0.3 * (X[:, :thr.SEL_VARIANTS] ** 2)
     M = np.ones_like(T, dtype=np.uint8)
     sel = thr.Selector(seed=6)
     sel.set_norm(np.zeros(16), np.ones(16))
@@ -108,7 +108,7 @@ def test_learned_policy_follows_the_model(small_index):
     qs = [(ids, int(rng.integers(0, len(ids) + 2))) for ids, _ in qs]
     sel = thr.Selector(seed=1)
     p = np.zeros(thr.SEL_PARAMS, np.float32)
-    p[-3:] = [1.0, 2.0, -1.0]  # W3 = 0: the model predicts ScanCount fastest
+    p[-4:] = [1.0, 2.0, -1.0, 3.0]  # W3 = 0: the model predicts ScanCount fastest
     sel.set_params(p)
     thr.set_selector(g, sel)
     try:
@@ -118,9 +118,17 @@ def test_learned_policy_follows_the_model(small_index):
         off, ln, pool = thr.thr_query_batch(g, qs, flags=thr.THR_POLICY_LEARNED)
         for k, (ids, T) in enumerate(qs):
             assert np.array_equal(pool[int(off[k]):int(off[k] + ln[k])], o.threshold(ids, T))
-        p[-3:] = [0.0, -1.0, 1.0]  # now the position-major decode wins
+        p[-4:] = [0.0, -1.0, 1.0, 2.0]  # now the position-major decode wins
         sel.set_params(p)
         assert thr.select_variants(g, qs, thr.THR_POLICY_LEARNED).tolist() == [1] * len(qs)
+        p[-4:] = [0.0, 1.0, 1.0, -0.05]  # split predicted 5% faster: below the margin
+        sel.set_params(p)
+        assert thr.select_variants(g, qs, thr.THR_POLICY_LEARNED).tolist() == [0] * len(qs)
+        p[-4:] = [0.0, 1.0, 1.0, -1.0]  # split clearly faster (where it applies)
+        sel.set_params(p)
+        off, ln, pool = thr.thr_query_batch(g, qs, flags=thr.THR_POLICY_LEARNED)
+        for k, (ids, T) in enumerate(qs):
+            assert np.array_equal(pool[int(off[k]):int(off[k] + ln[k])], o.threshold(ids, T))
     finally:
         thr.set_selector(g, None)
     # without a model the learned policy is the rule chooser
