@@ -295,6 +295,9 @@ int grid_for(uint32_t rows, int num_sms) {
 }  // namespace
 
 Selector::~Selector() {
+    cudaFree(pdev);
+    if (phost) cudaFreeHost(phost);
+    if (pst) cudaStreamDestroy(pst);
     cudaFree(p);
     cudaFree(g);
     cudaFree(m);
@@ -363,16 +366,33 @@ thr_status Selector::set_norm(const float* mean, const float* istd) {
 
 thr_status Selector::predict(const float* X, uint32_t rows, float* Y) const {
     if (!rows) return THR_OK;
-    DevData d;
-    CKM(d.upload(X, nullptr, nullptr, rows), "upload features");
-    float* dY = nullptr;
-    CKM(cudaMalloc(&dY, sizeof(float) * V * rows), "predictions");
-    k_mlp_forward<<<grid_for(rows, num_sms), H, kSmem>>>(d.X, norm, norm + F, p, q, bf16 ? 1 : 0,
-                                                         rows, dY);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpy(Y, dY, sizeof(float) * V * rows, cudaMemcpyDeviceToHost);
-    cudaFree(dY);
-    CKM(e, "MLP forward");
+    std::lock_guard<std::mutex> lk(pmu);
+    if (!pst) CKM(cudaStreamCreateWithFlags(&pst, cudaStreamNonBlocking), "predict stream");
+    if (pcap < rows) {
+        cudaFree(pdev);
+        if (phost) cudaFreeHost(phost);
+        pdev = nullptr;
+        phost = nullptr;
+        pcap = 0;
+        const uint32_t cap = std::max<uint32_t>(rows, 256);
+        CKM(cudaMalloc(&pdev, sizeof(float) * (F + V) * cap), "predict buffers");
+        CKM(cudaMallocHost(&phost, sizeof(float) * (F + V) * cap), "predict staging");
+        pcap = cap;
+    }
+    float* dX = pdev;
+    float* dY = pdev + size_t(F) * pcap;
+    float* hX = phost;
+    float* hY = phost + size_t(F) * pcap;
+    std::memcpy(hX, X, sizeof(float) * F * rows);
+    CKM(cudaMemcpyAsync(dX, hX, sizeof(float) * F * rows, cudaMemcpyHostToDevice, pst),
+        "upload features");
+    k_mlp_forward<<<grid_for(rows, num_sms), H, kSmem, pst>>>(dX, norm, norm + F, p, q,
+                                                                bf16 ? 1 : 0, rows, dY);
+    CKM(cudaGetLastError(), "MLP forward");
+    CKM(cudaMemcpyAsync(hY, dY, sizeof(float) * V * rows, cudaMemcpyDeviceToHost, pst),
+        "read predictions");
+    CKM(cudaStreamSynchronize(pst), "MLP forward");
+    std::memcpy(Y, hY, sizeof(float) * V * rows);
     return THR_OK;
 }
 

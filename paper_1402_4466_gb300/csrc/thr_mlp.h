@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/thr.h"
 
@@ -33,6 +34,13 @@ struct Selector {
     float* loss = nullptr;
     float h_norm[2 * kSelFeatures] = {};
     uint64_t step = 0;
+    // predict(): buffers kept between calls (grown on demand) and a stream,
+    // one caller at a time
+    mutable std::mutex pmu;
+    mutable float* pdev = nullptr;  // features | predictions
+    mutable float* phost = nullptr; // pinned staging of the same
+    mutable uint32_t pcap = 0;      // rows
+    mutable cudaStream_t pst = nullptr;
 
     ~Selector();
     thr_status init(uint64_t seed, bool use_bf16);
