@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -125,6 +126,70 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
     return std::strtoull(v, nullptr, 10);
 }
 
+// Groups among the chunk's grouped-carry-save queries over the same id
+// multiset: the first member leads, counts ones with enough slices for the
+// group's largest threshold and prunes only subtiles decided for every
+// member; the others are absorbed (no launch of their own).
+void form_groups(const BatchInput& in, uint32_t q0, uint32_t Q, std::vector<QDesc>& qd,
+                 std::vector<uint8_t>& qcls, std::vector<uint2>& grp,
+                 std::vector<uint32_t>& memb, std::vector<uint8_t>& absorbed) {
+    std::vector<std::pair<uint64_t, uint32_t>> keys;  // (hash of sorted ids, slot)
+    std::vector<std::vector<uint32_t>> sorted(Q);
+    for (uint32_t s = 0; s < Q; ++s) {
+        const uint32_t q = q0 + s;
+        if (class_family(qcls[q]) != 0) continue;
+        sorted[s].assign(in.ids + in.id_off[q], in.ids + in.id_off[q + 1]);
+        std::sort(sorted[s].begin(), sorted[s].end());
+        uint64_t h = fnv(14695981039346656037ull, sorted[s].size());
+        for (uint32_t v : sorted[s]) h = fnv(h, v);
+        keys.emplace_back(h, s);
+    }
+    std::sort(keys.begin(), keys.end());
+    int cnt = 0;
+    const KernelEntry* tab = kernel_table(&cnt);
+    for (size_t i = 0; i < keys.size();) {
+        size_t j = i + 1;
+        while (j < keys.size() && keys[j].first == keys[i].first) ++j;
+        // exact matches only (hash collisions stay apart)
+        std::vector<uint32_t> mem{keys[i].second};
+        for (size_t k = i + 1; k < j; ++k)
+            if (sorted[keys[k].second] == sorted[keys[i].second]) mem.push_back(keys[k].second);
+        i = j;
+        if (mem.size() < 2) continue;
+        std::sort(mem.begin(), mem.end());
+        const uint32_t n = qd[q0 + mem[0]].n;
+        uint32_t tlo = ~0u, thi = 0;
+        int need = 1;
+        for (uint32_t m : mem) {
+            const uint32_t T = qd[q0 + m].T;
+            tlo = std::min(tlo, T);
+            thi = std::max(thi, T);
+            if (T >= 1 && T <= n) {
+                int b = 0;
+                for (uint64_t v = T; v; v >>= 1) ++b;
+                need = std::max(need, b);
+            }
+        }
+        int c = -1;
+        for (int w = 0; w < cnt; ++w)
+            if (tab[w].S >= need) {
+                c = w;
+                break;
+            }
+        if (c < 0) continue;  // too wide for the counters: no sharing
+        const uint32_t lead = q0 + mem[0];
+        qd[lead].Tlo = tlo;
+        qd[lead].Thi = thi;
+        qd[lead].zmode = 0;  // ones are counted for every member
+        qcls[lead] = uint8_t(c);
+        grp[lead] = make_uint2(uint32_t(memb.size()), uint32_t(mem.size()));
+        for (uint32_t m : mem) {
+            memb.push_back(m);
+            if (q0 + m != lead) absorbed[q0 + m] = 1;
+        }
+    }
+}
+
 }  // namespace
 
 thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool, uint64_t cap,
@@ -159,9 +224,14 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         int cls = 0;
         uint32_t z = 0;
         resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls, &z);
-        qd[q] = QDesc{in.id_off[q], n, in.T[q], z};
+        qd[q] = QDesc{in.id_off[q], n, in.T[q], z, in.T[q], in.T[q]};
         qcls[q] = uint8_t(cls);
     }
+    // groups of queries over the same id multiset (grouped carry-save, same
+    // chunk): one counting pass serves them all (grp / memb, PassAParams)
+    std::vector<uint2> grp(nq, make_uint2(0, 1));
+    std::vector<uint32_t> memb;
+    std::vector<uint8_t> absorbed(nq, 0);
     int* per_sm = g_ctx.per_sm;
     // THR_TUNE_CONFIG=k in the environment forces configuration k (testing)
     const uint64_t env_cfg = env_u64("THR_TUNE_CONFIG", kTuneCandidates);
@@ -174,11 +244,13 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     for (uint32_t q0 = 0; q0 < nq; q0 += uint32_t(Qmax)) {
         const uint32_t Q = uint32_t(std::min<uint64_t>(Qmax, nq - q0));
         ChunkPlan ch{q0, Q, uint32_t(launches.size()), 0};
+        form_groups(in, q0, Q, qd, qcls, grp, memb, absorbed);
         // the chunk's shape and its launch configuration
         uint32_t present = 0;
         double sum_n = 0;
         int widest[4] = {-1, -1, -1, -1};  // per family
         for (uint32_t s = 0; s < Q; ++s) {
+            if (absorbed[q0 + s]) continue;
             const int c = qcls[q0 + s];
             present |= 1u << c;
             sum_n += qd[q0 + s].n;
@@ -198,6 +270,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         double work[kNumClasses] = {};
         double work_all = 0;
         for (uint32_t s = 0; s < Q; ++s) {  // cost ~ inputs x counter slices
+            if (absorbed[q0 + s]) continue;
             const int c = qcls[q0 + s];
             const double w =
                 double(qd[q0 + s].n) * (c == kClassScanCount ? 4.0 : 2.0 + class_width(c));
@@ -207,7 +280,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         for (int c = 0; c < kNumClasses; ++c) {
             const uint32_t off = uint32_t(lists.size());
             for (uint32_t s = 0; s < Q; ++s)
-                if (qcls[q0 + s] == c) lists.push_back(s);
+                if (qcls[q0 + s] == c && !absorbed[q0 + s]) lists.push_back(s);
             const uint32_t cnt = uint32_t(lists.size()) - off;
             if (!cnt) continue;
             if (!per_sm[c]) {  // once per thread and device
@@ -242,7 +315,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     const size_t o_qd = 0;
     const size_t o_ids = r256(sizeof(QDesc) * nq);
     const size_t o_lists = o_ids + r256(sizeof(uint32_t) * nids);
-    const size_t plan_bytes = o_lists + r256(sizeof(uint32_t) * lists.size());
+    const size_t o_grp = o_lists + r256(sizeof(uint32_t) * lists.size());
+    const size_t o_memb = o_grp + r256(sizeof(uint2) * nq);
+    const size_t plan_bytes = o_memb + r256(sizeof(uint32_t) * std::max<size_t>(memb.size(), 1));
     const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG, launches.size());
     const size_t res_bytes = 16 * size_t(nq) + 16;
     unsigned char* pin = nullptr;
@@ -250,6 +325,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     std::memcpy(pin + o_qd, qd.data(), sizeof(QDesc) * nq);
     std::memcpy(pin + o_ids, in.ids, sizeof(uint32_t) * nids);
     std::memcpy(pin + o_lists, lists.data(), sizeof(uint32_t) * lists.size());
+    std::memcpy(pin + o_grp, grp.data(), sizeof(uint2) * nq);
+    if (!memb.empty()) std::memcpy(pin + o_memb, memb.data(), sizeof(uint32_t) * memb.size());
     unsigned long long* h_res = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
 
     const bool graph = opt.graph && !opt.profile;
@@ -272,6 +349,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     b.qd = reinterpret_cast<const QDesc*>(dmem + o_qd);
     b.ids = reinterpret_cast<const uint32_t*>(dmem + o_ids);
     b.lists = reinterpret_cast<const uint32_t*>(dmem + o_lists);
+    b.grp = reinterpret_cast<const uint2*>(dmem + o_grp);
+    b.memb = reinterpret_cast<const uint32_t*>(dmem + o_memb);
     b.scratch = dmem + plan_bytes;
     b.lay = lay;
     b.out = dpool;

@@ -81,11 +81,16 @@ struct RangeAgg {
 constexpr int kAggWords = 8;
 
 // One query of a batch.  zmode 1: count the zeros of the active inputs.
+// Tlo, Thi: the thresholds pruning considers -- the query's own T, or for
+// the leader of a group of queries over the same id multiset (see
+// PassAParams::grp), which counts for all of them, the least and the
+// largest threshold of the group.
 struct QDesc {
     uint32_t ids_off;  // first id in the batch's id array
     uint32_t n;
     uint32_t T;
     uint32_t zmode;
+    uint32_t Tlo, Thi;
 };
 
 // Pass A of one launch: the queries (slots of the chunk) in list[0..nlist),
@@ -107,6 +112,11 @@ struct PassAParams {
     uint32_t ragged;  // r % 64
     uint64_t* U;      // scratch: slot s at U + s NG 128 (only non-uniform subtiles stored)
     uint32_t* aggs;   // scratch: slot s, subtile g at aggs + (s NG + g) kAggWords
+    // Queries sharing an id multiset: grp[s] = {first, count} of slot s's
+    // group in memb (the member slots; count 1 for a query on its own); the
+    // leader's warp counts once and compares for every member's threshold.
+    const uint2* grp;
+    const uint32_t* memb;
 };
 
 // Passes B and C of the re-encoding (thr_reencode.cu), over the Q slots of

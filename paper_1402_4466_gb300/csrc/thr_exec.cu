@@ -164,6 +164,8 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     for (uint32_t c = 0; c < nchunks; ++c) {
         const ChunkPlan& ch = chunks[c];
         p.qd = b.qd + ch.q0;
+        p.grp = b.grp + ch.q0;
+        p.memb = b.memb;
         const uint32_t nl = ch.l1 - ch.l0;
         // several launches run side by side on the aux streams
         const int nside = std::min<int>(int(nl) - 1, std::min(naux, nfork_ev - 1));

@@ -69,6 +69,8 @@ struct ExecBufs {
     const QDesc* qd;        // nq descriptors
     const uint32_t* ids;    // every id
     const uint32_t* lists;  // slot lists of all launches
+    const uint2* grp;       // nq: {first, count} of each query's group in memb
+    const uint32_t* memb;   // group member slots
     unsigned char* scratch; // ScratchLayout of the largest chunk
     ScratchLayout lay;
     uint64_t* out;          // output pool

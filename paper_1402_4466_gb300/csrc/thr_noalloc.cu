@@ -30,7 +30,8 @@ namespace {
 
 constexpr uint64_t kStaticMaxWords = 1ull << 20;  // r <= 2^26 rows
 constexpr uint64_t kStaticMaxIds = 65536;
-// fixed layout: query descriptor | slot list | ids | scratch of one slot
+// fixed layout: query descriptor | slot list, group record | ids | scratch
+// of one slot
 // (control words, aggregates, prefixes, result words: about 8.5 MiB at the
 // largest r)
 constexpr uint64_t kOffList = 256;
@@ -109,10 +110,13 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     int cls = 0;
     uint32_t zmode = 0;
     choose_class(n, T, &cls, &zmode);
-    const QDesc qd{0, n, T, zmode};
+    const QDesc qd{0, n, T, zmode, T, T};
+    const uint2 grp1 = make_uint2(0, 1);
     const uint32_t slot0 = 0;
     if ((e = cudaMemcpyAsync(blk, &qd, sizeof qd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(blk + kOffList, &slot0, sizeof slot0, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(blk + kOffList + 64, &grp1, sizeof grp1, cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(blk + kOffIds, ids, sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
                              st)) != cudaSuccess)
@@ -127,6 +131,8 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     ExecBufs b{};
     b.qd = reinterpret_cast<const QDesc*>(blk);
     b.lists = reinterpret_cast<const uint32_t*>(blk + kOffList);
+    b.grp = reinterpret_cast<const uint2*>(blk + kOffList + 64);
+    b.memb = reinterpret_cast<const uint32_t*>(blk + kOffList);
     b.ids = reinterpret_cast<const uint32_t*>(blk + kOffIds);
     b.scratch = blk + kOffScratch;
     b.lay = lay;

@@ -26,6 +26,7 @@ struct WarpSmem {
     unsigned long long woff[kCH];  // stream offsets of the current query's ids
     uint32_t ids[kCH];             //   and the ids, when n <= kCH
     uint32_t qn, qT, qz, qoff;     // the current query: n, T, zmode, first id
+    uint32_t qTx;                  //   largest threshold of its group (qT: the least)
 };
 
 struct CtaSmem {
@@ -40,6 +41,7 @@ struct QView {
     const uint32_t* all_ids;
     __device__ __forceinline__ uint32_t n() const { return w.qn; }
     __device__ __forceinline__ uint32_t T() const { return w.qT; }
+    __device__ __forceinline__ uint32_t Tmax() const { return w.qTx; }
     __device__ __forceinline__ uint32_t zmode() const { return w.qz; }
     __device__ __forceinline__ const uint32_t* ids() const { return all_ids + w.qoff; }
     __device__ __forceinline__ bool cached() const { return w.qn <= uint32_t(kCH); }
@@ -246,7 +248,7 @@ struct CsaCount {
 // policy (carry-save bit slices, or ScanCount counters).  kPos: mixed inputs
 // go through the position-major decode (ones counting; the host never sets
 // zmode for these kernels), literal runs through the grouped one.
-// Counting part of subtile_result: classify the query's inputs over the
+// Counting part of a subtile's result: classify the query's inputs over the
 // subtile, count k (ones fills) and d (inputs with literals) and add the
 // active inputs into `count`.  kPart: the inputs are one part of a query
 // whose other parts other warps count, so the totals are not known and the
@@ -270,8 +272,8 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
             k_ones += __popc(__ballot_sync(~0u, cls == 1));
             d_act += __popc(__ballot_sync(~0u, cls >= 2));
         }
-        const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
-        pruned = Tp <= 0 || Tp > int64_t(d_act);
+        pruned = int64_t(q.Tmax()) <= int64_t(k_ones) ||
+                 int64_t(q.T()) - int64_t(k_ones) > int64_t(d_act);
     }
     for (uint32_t c0 = 0; c0 < q.n() && !pruned; c0 += kCH) {
         const uint32_t cn = min(uint32_t(kCH), q.n() - c0);
@@ -317,8 +319,10 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
         __syncwarp();
         if (one_chunk) {  // run-aware pruning (Sec. 6.4 cases 1 and 2)
             d_act = nrec;
-            const int64_t Tp = int64_t(q.T()) - int64_t(k_ones);
-            if (!kPart && (Tp <= 0 || Tp > int64_t(d_act))) break;
+            // decided for every threshold of the group: all ones or all zeros
+            if (!kPart && (int64_t(q.Tmax()) <= int64_t(k_ones) ||
+                           int64_t(q.T()) - int64_t(k_ones) > int64_t(d_act)))
+                break;
         } else if (kPart) {
             d_act += nrec;
         }
@@ -381,15 +385,6 @@ __device__ __forceinline__ void finish_subtile(const PassAParams& p, uint32_t T,
     }
 }
 
-template <class Count, bool kPos = false>
-__device__ __forceinline__ void subtile_result(const PassAParams& p, const QView& q,
-                                               uint32_t x0, uint32_t x1, uint32_t lane,
-                                               WarpSmem& ws, Count& count,
-                                               uint64_t (&o)[kRows]) {
-    uint32_t k_ones = 0, d_act = 0;
-    count_subtile<Count, kPos, false>(p, q, x0, x1, lane, ws, count, k_ones, d_act);
-    finish_subtile(p, q.T(), q.zmode(), k_ones, d_act, x0, lane, count, o);
-}
 
 // Canonical re-encoding, part 1 (per subtile, by its warp).  o[q] is word
 // xb + q, xb = x0 + 4 lane.  Word classes (0 zero, 1 ones, 2 literal) give
@@ -483,13 +478,14 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
 // cached in the warp's shared memory when n <= kCH.
 __device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, uint32_t ids_off,
                                            uint32_t n, uint32_t T, uint32_t zmode,
-                                           uint32_t lane) {
+                                           uint32_t Tmax, uint32_t lane) {
     __syncwarp();
     if (lane == 0) {
         ws.qn = n;
         ws.qT = T;
         ws.qz = zmode;
         ws.qoff = ids_off;
+        ws.qTx = Tmax;
     }
     if (n <= uint32_t(kCH)) {
         for (uint32_t i = lane; i < n; i += 32) {
@@ -539,6 +535,7 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
     const uint32_t nwarps = gridDim.x * kNW;
     const uint32_t nitems = p.nlist * p.NG;
     uint32_t cur = ~0u;  // slot whose ids the warp holds
+    uint2 grp = make_uint2(0, 1);
     const QView q{ws, p.ids};
     // static striding, or items taken from the launch's counter one at a
     // time (the next one is requested while the current one runs)
@@ -562,14 +559,25 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
         const uint32_t s = __ldg(p.list + li);
         if (s != cur) {  // a new query: its parameters, and its ids when they fit
             const QDesc d = p.qd[s];
-            load_query(p, ws, d.ids_off, d.n, d.T, d.zmode, lane);
+            load_query(p, ws, d.ids_off, d.n, d.Tlo, d.zmode, d.Thi, lane);
+            grp = p.grp[s];
             cur = s;
         }
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint64_t orow[kRows];
-        subtile_result<Count, kPos>(p, q, x0, x1, lane, ws, count, orow);
-        store_subtile(p, ws, cur, g, x0, x1, lane, orow);
+        uint32_t k_ones = 0, d_act = 0;
+        count_subtile<Count, kPos, false>(p, q, x0, x1, lane, ws, count, k_ones, d_act);
+        if (grp.y <= 1) {
+            finish_subtile(p, q.T(), q.zmode(), k_ones, d_act, x0, lane, count, orow);
+            store_subtile(p, ws, cur, g, x0, x1, lane, orow);
+        } else {  // one count, every member's threshold (ones counted)
+            for (uint32_t i = 0; i < grp.y; ++i) {
+                const uint32_t m = __ldg(p.memb + grp.x + i);
+                finish_subtile(p, p.qd[m].T, 0u, k_ones, d_act, x0, lane, count, orow);
+                store_subtile(p, ws, m, g, x0, x1, lane, orow);
+            }
+        }
         it = p.work ? __shfl_sync(~0u, next, 0) : it + nwarps;
     }
 }
@@ -617,7 +625,7 @@ __global__ void __launch_bounds__(kNT, 4) k_threshold_split(const PassAParams p)
             const QDesc d = p.qd[s];
             const uint32_t a = uint32_t(uint64_t(d.n) * wid / kNW);
             const uint32_t b = uint32_t(uint64_t(d.n) * (wid + 1) / kNW);
-            load_query(p, ws, d.ids_off + a, b - a, d.T, d.zmode, lane);
+            load_query(p, ws, d.ids_off + a, b - a, d.T, d.zmode, d.T, lane);
             T = d.T;
             zmode = d.zmode;
             cur = s;

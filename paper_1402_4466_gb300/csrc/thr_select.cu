@@ -90,6 +90,18 @@ uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
     return uint8_t(best);
 }
 
+// The split-input kernel buys parallelism for queries with few subtiles; a
+// batch whose (query, subtile) items already outnumber the GPU's resident
+// warps several times over gains nothing from it (the costs both choosers
+// learned come from queries timed alone), so it is not chosen there.
+void drop_split_when_saturated(const thr_index* idx, uint32_t nq, std::vector<uint8_t>* var) {
+    const uint64_t items = uint64_t(nq) * idx->NG;
+    const uint64_t warps = uint64_t(std::max(idx->num_sms, 1)) * 6 * kNW;  // resident
+    if (nq > 1 && items >= 4 * warps)
+        for (auto& v : *var)
+            if (v == kVarSplit) v = uint8_t(kVarCsa);
+}
+
 int variant_of_flag(uint32_t f) {
     switch (f) {
         case THR_VARIANT_CSA: return kVarCsa;
@@ -112,10 +124,15 @@ thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id
     if (policy == THR_POLICY_LEARNED) {
         bool used = false;
         thr_status s = learned_choice(idx, nq, id_off, ids, T, cls, &used);
-        if (s != THR_OK || used) return s;
+        if (s != THR_OK) return s;
+        if (used) {
+            drop_split_when_saturated(idx, nq, cls);
+            return THR_OK;
+        }
     }
     for (uint32_t q = 0; q < nq; ++q)
         (*cls)[q] = rule_choice(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q]);
+    drop_split_when_saturated(idx, nq, cls);
     return THR_OK;
 }
 

@@ -169,13 +169,16 @@ def test_batch_pool_too_small(mixed):
 
 def test_batch_many_criteria_full_size(many_criteria_full):
     """The 64 x 2^26 many-criteria bitmaps, the four thresholds as one batch
-    (several kernel classes side by side), against the oracle."""
+    (one counting pass shared by the four: same inputs) plus a query over
+    other inputs (a second kernel class side by side), against the oracle."""
     arrays, r = many_criteria_full
     g, o = _index(arrays, r)
     ids = np.arange(synth.MANY_N, dtype=np.uint32)
-    qs = [(ids, T) for T in synth.MANY_TS]
+    qs = [(ids, T) for T in synth.MANY_TS] + [(ids[:40], 2)]
     off, ln, pool = thr.thr_query_batch(g, qs)
-    assert thr.thr_last_batch_info()["launches"] >= 2
+    assert thr.thr_last_batch_info()["launches"] == 2
+    _check(g, o, qs, off, ln, pool)
+    off, ln, pool = thr.thr_query_batch(g, qs, flags=thr.THR_NO_GRAPH)
     _check(g, o, qs, off, ln, pool)
 
 
@@ -201,4 +204,27 @@ def test_autotune_keeps_the_fastest(mixed):
     off, ln, pool = thr.thr_query_batch(g, qs)
     assert thr.thr_last_batch_info()["config"] == best
     assert np.array_equal(ln, before[1])
+    _check(g, o, qs, off, ln, pool)
+
+
+def test_queries_sharing_inputs_count_once(mixed, monkeypatch):
+    """Queries over the same id multiset (in any order, with repeats) share
+    one counting pass: results per threshold equal the oracle's, every
+    threshold kind included (0, 1, close to n, n, n + 1), and the group needs
+    one pass-A launch."""
+    g, o, r = mixed
+    rng = np.random.default_rng(41)
+    base = rng.integers(0, 48, 30).astype(np.uint32)
+    qs = []
+    for T in (0, 1, 2, 5, 15, 28, 29, 30, 31):
+        qs.append((rng.permutation(base), T))
+    other = rng.integers(0, 48, 12).astype(np.uint32)
+    qs += [(other, 3), (np.concatenate([other, other[:2]]), 3)]  # not the same multiset
+    off, ln, pool = thr.thr_query_batch(g, qs)
+    _check(g, o, qs, off, ln, pool)
+    # one launch counts the group (5-bit counters for T <= 30), one the rest
+    assert thr.thr_last_batch_info()["launches"] <= 2
+    # groups never span chunks: with 4 slots per chunk the results still hold
+    monkeypatch.setenv("THR_MAX_SLOTS", "4")
+    off, ln, pool = thr.thr_query_batch(g, qs)
     _check(g, o, qs, off, ln, pool)
