@@ -67,6 +67,9 @@ def parse():
                          "then one more (the launch to capture with a profiler); no timing")
     ap.add_argument("--variant", default="csa", choices=["csa", "position", "scancount"],
                     help="counting variant of --profile-query")
+    ap.add_argument("--batch", action="store_true",
+                    help="with --profile-query: the step's four thresholds as one batched "
+                         "call (shared counting pass) instead of one query")
     return ap.parse_args()
 
 
@@ -223,6 +226,14 @@ def run_ours(args):
             out_words[T] = int(n)
         return ev0.elapsed_time(ev1)
 
+    def batched_call(flags):
+        flushed()
+        ev0.record(stream)
+        thr.thr_query_batch(idx, qs, pool=pool, flags=flags, stream=stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
     def plain_query(T, flags=0):
         flushed()
         ev0.record(stream)
@@ -235,6 +246,7 @@ def run_ours(args):
     # launch configurations of this workload's shapes (autotuner)
     single_cfg, single_tune_ms = thr.thr_autotune(idx, [qs[0]], reps=3, stream=stream)
     batch_cfg, batch_tune_ms = thr.thr_autotune(idx, qs, flags=POLICY, reps=3, stream=stream)
+    thr.thr_autotune(idx, qs, flags=POLICY | thr.THR_NO_SHARE, reps=3, stream=stream)
 
     uuid = None
     try:
@@ -263,6 +275,12 @@ def run_ours(args):
     nq = len(Ts) * args.steps * world
     value = nq / (total_ms / 1e3)
     input_gbs = (in_bytes * nq) / (total_ms / 1e3) / 1e9
+
+    # the same batch without the shared counting pass (each query counts its
+    # own inputs), and the pass-A time of the batched step (THR_PROFILE)
+    nos_ms = [batched_call(POLICY | thr.THR_NO_SHARE) for _ in range(args.steps)]
+    thr.thr_query_batch(idx, qs, pool=pool, flags=POLICY | thr.THR_PROFILE, stream=stream)
+    step_pass_a_ms = thr.thr_last_kernel_ms()
 
     # plain: one thr_query per query (default variant), and the pass-A
     # kernel time of each (the roofline's launch)
@@ -332,6 +350,19 @@ def run_ours(args):
         "plain": {"value": round(plain_value, 3), "unit": "queries/s",
                   "what": "one thr_query per query, default variant, CUDA events per call",
                   "batched_speedup": round(value / plain_value, 3)},
+        "batched_without_sharing": {
+            "value": round(len(Ts) * len(nos_ms) / (sum(nos_ms) / 1e3), 3), "unit": "queries/s",
+            "what": "the same batched call with THR_NO_SHARE: every query counts its own "
+                    "inputs (the default shares one counting pass among queries over the "
+                    "same id multiset)"},
+        "roofline_step": {
+            "what": "pass A of the batched step: one launch counting the four queries' "
+                    "shared inputs once",
+            "pass_a_ms": round(step_pass_a_ms, 5),
+            "credited_bytes": 4 * in_bytes + 8 * sum(out_words.values()),
+            "credited_gbs": round((4 * in_bytes + 8 * sum(out_words.values())) /
+                                  (step_pass_a_ms / 1e3) / 1e9, 1),
+            "input_bytes_read_once": in_bytes},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": ncu_traffic(), "peak_kind": peak_kind,
@@ -433,8 +464,14 @@ def profile_query(args):
             "scancount": thr.THR_VARIANT_SCANCOUNT}[args.variant]
     ids = np.arange(synth.MANY_N, dtype=np.uint32)
     dout = torch.empty(idx.nwords + 1, dtype=torch.int64, device="cuda")
+    pool = torch.empty(4 * (idx.nwords + 1), dtype=torch.int64, device="cuda")
     for _ in range(2):
-        n = thr.thr_query(idx, ids, args.profile_query, out=dout, flags=flag)
+        if args.batch:
+            _, ln, _ = thr.thr_query_batch(idx, [(ids, T) for T in synth.MANY_TS], pool=pool,
+                                           flags=flag | thr.THR_NO_GRAPH)
+            n = int(ln.sum())
+        else:
+            n = thr.thr_query(idx, ids, args.profile_query, out=dout, flags=flag)
     torch.cuda.synchronize()
     print(json.dumps({"profile_query": args.profile_query, "variant": args.variant,
                       "output_words": n, "input_bytes": 8 * int(goff[-1])}))

@@ -68,6 +68,8 @@ typedef enum {
 #define THR_POLICY_MASK 0xF0u
 #define THR_PROFILE 0x100u      /* time the query kernel with CUDA events */
 #define THR_NO_GRAPH 0x1000u    /* batch: launch directly, no CUDA graph */
+#define THR_NO_SHARE 0x2000u    /* batch: no shared counting pass for queries
+                                   over the same id multiset */
 /* Counting kernel of a query (thr_query; thr_query_batch with
  * THR_POLICY_PLAIN uses it for every query):
  *   THR_VARIANT_CSA        carry-save bit-sliced counters in registers
@@ -262,7 +264,8 @@ double thr_last_kernel_ms(void);
 
 /*
  * Autotuner of the batched launch.  Runs the sample batch (arguments as for
- * thr_query_batch; flags: a THR_POLICY_* value and THR_VARIANT_* only) under
+ * thr_query_batch; flags: a THR_POLICY_* and THR_VARIANT_* value, and
+ * THR_NO_SHARE to tune batches that run without shared counting) under
  * each of the 16 launch configurations of pass A, reps times each after one
  * warm-up run, with L2 flushed before every run, and keeps the fastest for
  * the batch's shape (several kernel classes or one; mean inputs per query)

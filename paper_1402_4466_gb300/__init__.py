@@ -26,6 +26,7 @@ THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
 THR_NO_GRAPH = 0x1000
+THR_NO_SHARE = 0x2000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 THR_VARIANT_SPLIT = 0x600
 

@@ -240,11 +240,11 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     std::vector<uint32_t> lists;
     lists.reserve(nq);
     uint64_t key = fnv(14695981039346656037ull, nq > 0 ? 1 : 0);
-    uint32_t first_cfg = 0;
+    uint32_t first_cfg = 0, first_key = 0;
     for (uint32_t q0 = 0; q0 < nq; q0 += uint32_t(Qmax)) {
         const uint32_t Q = uint32_t(std::min<uint64_t>(Qmax, nq - q0));
         ChunkPlan ch{q0, Q, uint32_t(launches.size()), 0};
-        form_groups(in, q0, Q, qd, qcls, grp, memb, absorbed);
+        if (opt.share) form_groups(in, q0, Q, qd, qcls, grp, memb, absorbed);
         // the chunk's shape and its launch configuration
         uint32_t present = 0;
         double sum_n = 0;
@@ -257,8 +257,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
             widest[class_family(c)] = std::max(widest[class_family(c)], c);
         }
         const bool multi = __builtin_popcount(present) > 1;
-        uint32_t cfg = opt.force_tune >= 0 ? uint32_t(opt.force_tune)
-                                           : tune_lookup(idx, tune_key(multi, sum_n / Q));
+        const uint32_t shape = tune_key(multi, sum_n / Q);
+        if (q0 == 0) first_key = shape;
+        uint32_t cfg = opt.force_tune >= 0 ? uint32_t(opt.force_tune) : tune_lookup(idx, shape);
         if (opt.force_tune < 0 && env_cfg < kTuneCandidates) cfg = uint32_t(env_cfg);
         if (q0 == 0) first_cfg = cfg;
         if (cfg & kTuneMerge) {  // one counter width per carry-save family
@@ -308,6 +309,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         stats->launches = uint32_t(launches.size());
         stats->slots = uint32_t(Qmax);
         stats->tune = first_cfg;
+        stats->tune_key = first_key;
     }
 
     // ---- device memory: plan (descriptors, ids, lists) | scratch

@@ -27,11 +27,13 @@ struct BatchOptions {
     bool profile = false;      // time the pass-A launches (no graph then)
     uint64_t scratch_bytes = 0;  // scratch budget per batch; 0: from free memory
     int force_tune = -1;       // launch configuration for every chunk (tuner)
+    bool share = true;         // one counting pass per group of queries over the same ids
 };
 
 struct BatchStats {
     uint32_t chunks = 0, launches = 0, slots = 0;
     uint32_t tune = 0;      // configuration of the first chunk
+    uint32_t tune_key = 0;  // its shape key (tune_key)
     int graph_reused = -1;  // 1 updated a cached graph, 0 instantiated, -1 no graph
     double pass_a_ms = -1;  // with profile
 };
@@ -64,7 +66,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
 // Time every launch configuration on the sample batch (reps runs each after
 // a warm-up, L2 flushed before each) and store the fastest for its shape.
 thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st, uint32_t reps,
-                    double* times, uint32_t* best);
+                    double* times, uint32_t* best, bool share);
 
 // Counting variant per query for a thr_query_batch policy (thr_select.cu);
 // variant_flag: the THR_VARIANT_* of the flags (THR_POLICY_PLAIN).

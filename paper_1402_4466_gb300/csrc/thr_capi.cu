@@ -509,12 +509,14 @@ thr_status thr_autotune(const thr_index* idx, uint32_t nq, const uint32_t* id_of
                         void* cuda_stream, double* times, uint32_t* best) {
     if (nq == 0) return fail(THR_E_INVAL, "empty sample batch");
     if (reps == 0) return fail(THR_E_INVAL, "reps must be at least 1");
-    if (flags & ~(THR_POLICY_MASK | THR_VARIANT_MASK)) return fail(THR_E_INVAL, "unknown flags");
+    if (flags & ~(THR_POLICY_MASK | THR_VARIANT_MASK | THR_NO_SHARE))
+        return fail(THR_E_INVAL, "unknown flags");
     std::vector<uint8_t> cls;
-    thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &cls);
+    thr_status ps = check_batch(idx, nq, id_off, ids, T, flags & ~THR_NO_SHARE, &cls);
     if (ps != THR_OK) return ps;
     BatchInput in{nq, id_off, ids, T, cls.data()};
-    return autotune(idx, in, (cudaStream_t)cuda_stream, reps, times, best);
+    return autotune(idx, in, (cudaStream_t)cuda_stream, reps, times, best,
+                    !(flags & THR_NO_SHARE));
 }
 
 thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
@@ -525,7 +527,7 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
         return fail(THR_E_INVAL, "null argument");
     if (nq == 0) return THR_OK;
     if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK |
-                  THR_NO_GRAPH))
+                  THR_NO_GRAPH | THR_NO_SHARE))
         return fail(THR_E_INVAL, "unknown flags");
     std::vector<uint8_t> cls;
     thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &cls);
@@ -534,6 +536,7 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
     BatchOptions opt;
     opt.graph = !(flags & THR_NO_GRAPH);
     opt.profile = flags & THR_PROFILE;
+    opt.share = !(flags & THR_NO_SHARE);
     BatchStats stats;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t total = 0;

@@ -27,7 +27,7 @@ uint32_t tune_lookup(const thr_index* idx, uint32_t key) {
 }
 
 thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st, uint32_t reps,
-                    double* times, uint32_t* best) {
+                    double* times, uint32_t* best, bool share) {
     // flush buffer: every timed run starts with inputs out of L2
     const size_t flush_bytes = size_t(256) << 20;
     void* flush = nullptr;
@@ -43,12 +43,13 @@ thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st,
     std::vector<uint64_t> off(in.nq), len(in.nq);
     uint64_t total = 0;
     double t_best = 1e300;
-    uint32_t c_best = 0;
+    uint32_t c_best = 0, key = 0;
     thr_status rs = THR_OK;
     for (uint32_t c = 0; c < kTuneCandidates && rs == THR_OK; ++c) {
         BatchOptions opt;
         opt.graph = true;
         opt.force_tune = int(c);
+        opt.share = share;
         std::vector<double> t;
         for (uint32_t k = 0; k < reps + 1 && rs == THR_OK; ++k) {  // first run warms up
             if ((e = cudaMemsetAsync(flush, k & 0xFF, flush_bytes, st)) != cudaSuccess ||
@@ -56,9 +57,11 @@ thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st,
                 rs = report_error(THR_E_CUDA, "autotune: flush");
                 break;
             }
+            BatchStats stats;
             const auto t0 = std::chrono::steady_clock::now();
-            rs = run_batch(idx, in, pool, cap, off.data(), len.data(), &total, st, opt, nullptr);
+            rs = run_batch(idx, in, pool, cap, off.data(), len.data(), &total, st, opt, &stats);
             const auto t1 = std::chrono::steady_clock::now();
+            key = stats.tune_key;  // the shape as the batch's planning sees it
             if (k) t.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
         }
         if (rs != THR_OK) break;
@@ -75,17 +78,6 @@ thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st,
     cudaStreamSynchronize(st);
     if (rs != THR_OK) return rs;
     // store the winner for the shape of the sample's first chunk
-    int cls0 = 0;
-    uint32_t present = 0;
-    double sum_n = 0;
-    for (uint32_t q = 0; q < in.nq; ++q) {
-        const uint32_t n = in.id_off[q + 1] - in.id_off[q];
-        uint32_t z = 0;
-        resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls0, &z);
-        present |= 1u << cls0;
-        sum_n += n;
-    }
-    const uint32_t key = tune_key(__builtin_popcount(present) > 1, sum_n / std::max(1u, in.nq));
     {
         std::lock_guard<std::mutex> lk(idx->tune_mu);
         idx->tune[key] = c_best;

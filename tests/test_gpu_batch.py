@@ -224,6 +224,10 @@ def test_queries_sharing_inputs_count_once(mixed, monkeypatch):
     _check(g, o, qs, off, ln, pool)
     # one launch counts the group (5-bit counters for T <= 30), one the rest
     assert thr.thr_last_batch_info()["launches"] <= 2
+    # without sharing: the same results, every query counting for itself
+    off2, ln2, pool2 = thr.thr_query_batch(g, qs, flags=thr.THR_NO_SHARE)
+    assert np.array_equal(ln, ln2)
+    assert np.array_equal(pool[: int(ln.sum())], pool2[: int(ln2.sum())])
     # groups never span chunks: with 4 slots per chunk the results still hold
     monkeypatch.setenv("THR_MAX_SLOTS", "4")
     off, ln, pool = thr.thr_query_batch(g, qs)
