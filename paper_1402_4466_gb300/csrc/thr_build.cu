@@ -239,6 +239,29 @@ __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
     sdesc[i] = (sd & ((1ull << 19) - 1)) | (idx << 19);
 }
 
+// Thread per (bitmap, word): the classes of 32 consecutive subtiles.
+__global__ void k_pack_classes(const uint64_t* __restrict__ sdesc, uint64_t* __restrict__ pcls,
+                               uint32_t nbitmaps, uint32_t NG, uint32_t NGW) {
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= uint64_t(nbitmaps) * NGW) return;
+    const uint64_t b = i / NGW;
+    const uint32_t w = uint32_t(i - b * NGW);
+    uint64_t word = 0;
+    for (uint32_t k = 0; k < 32; ++k) {
+        const uint32_t g = 32 * w + k;
+        if (g < NG) word |= (sdesc[b * NG + g] & 3ull) << (2 * k);
+    }
+    pcls[i] = word;
+}
+
+cudaError_t launch_pack_classes(const uint64_t* sdesc, uint64_t* pcls, uint32_t nbitmaps,
+                                uint32_t NG, cudaStream_t st) {
+    const uint32_t NGW = (NG + 31) / 32;
+    const uint64_t n = uint64_t(nbitmaps) * NGW;
+    k_pack_classes<<<unsigned((n + 255) / 256), 256, 0, st>>>(sdesc, pcls, nbitmaps, NG, NGW);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
                                  const BitmapDesc* desc, uint2* mtab, uint32_t* ttab,
                                  uint64_t* sdesc, uint32_t* mixed_count,

@@ -400,6 +400,9 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
     if (e == cudaSuccess)
         e = launch_index_build_b(idx->d_mtab, d_ttab, idx->d_desc, d_mbase, idx->d_sdesc,
                                  idx->d_masks, nbitmaps, idx->W, idx->NG, st);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&idx->d_pcls, sizeof(uint64_t) * uint64_t(nbitmaps) * ((idx->NG + 31) / 32));
+    if (e == cudaSuccess) e = launch_pack_classes(idx->d_sdesc, idx->d_pcls, nbitmaps, idx->NG, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     free_all_tmp();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "index build kernels"));
@@ -416,6 +419,7 @@ void idx_free(thr_index* idx) {
     cudaFree(idx->d_words);
     cudaFree(idx->d_mtab);
     cudaFree(idx->d_sdesc);
+    cudaFree(idx->d_pcls);
     cudaFree(idx->d_masks);
     cudaFree(idx->d_desc);
     cudaSetDevice(cur);

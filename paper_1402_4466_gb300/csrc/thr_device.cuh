@@ -12,6 +12,9 @@
 //          of the bitmap over the subtile (zero fill, ones fill, one literal
 //          run, mixed) and, for a literal run, the stream index of its first
 //          literal, for a mixed subtile the index of its mask record.
+//   pcls   the classes of sdesc packed 2 bits each, 32 subtiles per uint64,
+//          ceil(NG / 32) words per bitmap: classification reads these and
+//          the full descriptor only for inputs with literals.
 //   masks  one 64-byte MaskRec per mixed (bitmap, subtile).
 //
 // A query (or a batch of them) runs in three passes:
@@ -99,6 +102,7 @@ struct QDesc {
 struct PassAParams {
     const uint64_t* words;
     const uint64_t* sdesc;  // subtile descriptors, NG per bitmap
+    const uint64_t* pcls;   // packed subtile classes, NGW words per bitmap
     const MaskRec* masks;   // mask records of the mixed subtiles
     const BitmapDesc* desc;
     const QDesc* qd;        // the chunk's queries, by slot
@@ -109,6 +113,7 @@ struct PassAParams {
     uint32_t* work;   // item counter (zeroed before the launch), or null: static striding
     uint32_t W;       // uncompressed words
     uint32_t NG;      // subtiles
+    uint32_t NGW;     // packed class words per bitmap, ceil(NG / 32)
     uint32_t ragged;  // r % 64
     uint64_t* U;      // scratch: slot s at U + s NG 128 (only non-uniform subtiles stored)
     uint32_t* aggs;   // scratch: slot s, subtile g at aggs + (s NG + g) kAggWords
@@ -331,6 +336,9 @@ cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
                                  uint64_t* sdesc, uint32_t* mixed_count,
                                  uint32_t nbitmaps, uint32_t W, uint32_t NG,
                                  cudaStream_t st);
+// Packed classes from the final subtile descriptors (after part b).
+cudaError_t launch_pack_classes(const uint64_t* sdesc, uint64_t* pcls, uint32_t nbitmaps,
+                                uint32_t NG, cudaStream_t st);
 cudaError_t launch_index_build_b(const uint2* mtab, const uint32_t* ttab,
                                  const BitmapDesc* desc, const uint64_t* mixed_base,
                                  uint64_t* sdesc, MaskRec* masks, uint32_t nbitmaps,

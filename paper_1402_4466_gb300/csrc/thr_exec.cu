@@ -137,6 +137,8 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     PassAParams p{};
     p.words = idx->d_words;
     p.sdesc = idx->d_sdesc;
+    p.pcls = idx->d_pcls;
+    p.NGW = (NG + 31) / 32;
     p.masks = idx->d_masks;
     p.desc = idx->d_desc;
     p.ids = b.ids;

@@ -25,6 +25,7 @@ struct thr_index {
     uint64_t* d_words = nullptr;
     uint2* d_mtab = nullptr;
     uint64_t* d_sdesc = nullptr;  // NG subtile descriptors per bitmap
+    uint64_t* d_pcls = nullptr;   // their classes, 2 bits each, ceil(NG/32) words per bitmap
     thr::MaskRec* d_masks = nullptr;  // mask records of the mixed subtiles
     uint64_t mixed_subtiles = 0;
     thr::BitmapDesc* d_desc = nullptr;

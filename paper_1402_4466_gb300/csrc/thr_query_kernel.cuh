@@ -268,7 +268,9 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
         for (uint32_t i0 = 0; i0 < q.n(); i0 += 32) {
             const uint32_t i = i0 + lane;
             uint32_t cls = 0;
-            if (i < q.n()) cls = uint32_t(__ldg(p.sdesc + uint64_t(__ldg(q.ids() + i)) * p.NG + g) & 3u);
+            if (i < q.n())
+                cls = uint32_t(__ldg(p.pcls + uint64_t(__ldg(q.ids() + i)) * p.NGW + (g >> 5)) >>
+                               (2 * (g & 31))) & 3u;
             k_ones += __popc(__ballot_sync(~0u, cls == 1));
             d_act += __popc(__ballot_sync(~0u, cls >= 2));
         }
@@ -285,9 +287,10 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
             uint4 r = make_uint4(0, 0, 0, 0);
             if (i < cn) {
                 const uint32_t b = q.cached() ? ws.ids[i] : __ldg(q.ids() + c0 + i);
-                const uint64_t sd = __ldg(p.sdesc + uint64_t(b) * p.NG + g);
-                cls = uint32_t(sd & 3u);
+                // the packed class first; the full descriptor only for inputs with literals
+                cls = uint32_t(__ldg(p.pcls + uint64_t(b) * p.NGW + (g >> 5)) >> (2 * (g & 31))) & 3u;
                 if (cls >= 2) {
+                    const uint64_t sd = __ldg(p.sdesc + uint64_t(b) * p.NG + g);
                     const uint64_t woff = q.cached() ? ws.woff[i] : p.desc[b].woff;
                     const uint64_t field = sd >> 19;
                     if (cls == 2) {
