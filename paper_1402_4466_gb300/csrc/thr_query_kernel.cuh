@@ -506,6 +506,20 @@ __device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, u
 __device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws, uint32_t slot,
                                               uint32_t g, uint32_t x0, uint32_t x1,
                                               uint32_t lane, const uint64_t (&orow)[kRows]) {
+    const uint64_t sg = uint64_t(slot) * p.NG + g;
+    // one fill class over all 128 words (words past W are zero): no head and
+    // no literal inside, the aggregate follows without the scan
+    const uint64_t any = orow[0] | orow[1] | orow[2] | orow[3];
+    const uint64_t all = orow[0] & orow[1] & orow[2] & orow[3];
+    const bool zeros = __all_sync(~0u, any == 0);
+    const bool ones = __all_sync(~0u, all == ~0ull);
+    if (zeros || ones) {
+        if (lane == 0) {
+            const uint32_t c = ones ? 1u : 0u;
+            agg_store_plain(p.aggs + sg * kAggWords, RangeAgg{x0, 0, 0, 0, 0, c | (c << 2)});
+        }
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) ws.tw[32 * r + lane] = orow[r];
     __syncwarp();
@@ -514,7 +528,6 @@ __device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws
     for (int k = 0; k < kWPL; ++k) o[k] = ws.tw[kWPL * lane + k];
     __syncwarp();
     const LocalScan L = local_scan(x0, x1, lane, o);
-    const uint64_t sg = uint64_t(slot) * p.NG + g;
     if (L.A.nh || L.A.nl) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) p.U[sg * kGW + 32 * r + lane] = orow[r];

@@ -252,24 +252,10 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
     const uint32_t x1 = min(x0 + uint32_t(kGW), w.W);
     const uint32_t xb = x0 + kWPL * lane;
     const RangeAgg A = agg_load_plain(w.aggs + sg * kAggWords);
-    uint64_t o[kWPL];
-    if (A.nh || A.nl) {
-        const ulonglong2* src =
-            reinterpret_cast<const ulonglong2*>(w.U + uint64_t(s) * w.NG * kGW + xb);
-        const ulonglong2 a = src[0], b = src[1];
-        o[0] = a.x;
-        o[1] = a.y;
-        o[2] = b.x;
-        o[3] = b.y;
-    } else {  // one fill class over the whole subtile
-        const uint64_t f = agg_fc(A) == 1u ? ~0ull : 0ull;
-#pragma unroll
-        for (int q = 0; q < kWPL; ++q) o[q] = f;
-    }
-    const LocalScan L = local_scan(x0, x1, lane, o);
+    // prefix before the subtile, and whether its first word starts a group
     RangeAgg P;
     uint32_t hf;
-    const uint32_t fc = L.A.cls & 3u;
+    const uint32_t fc = agg_fc(A);
     if (g == 0) {
         P.start = P.nh = P.nl = P.lh = P.lp = P.cls = 0;
         hf = 1;
@@ -285,6 +271,30 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
         }
         hf = starts_group(agg_lc(P), fc) ? 1u : 0u;
     }
+    if (!(A.nh || A.nl)) {
+        // one fill class over the whole subtile: no literal and no group start
+        // inside it; only the group that ends at its first word (when that
+        // word starts a new group) gets its marker
+        if (g > 0 && hf && lane == 0 && agg_has(P)) {
+            const uint64_t Lw = uint64_t(P.nl) - P.lp;
+            const uint64_t F = uint64_t(x0 - P.lh) - Lw;
+            const uint64_t bit = (F && agg_lhc(P) == 1u) ? 1ull : 0ull;
+            const uint64_t pos = off + uint64_t(P.nh) - 1 + P.lp;
+            if (pos < w.cap) w.out[pos] = bit | (F << 1) | (Lw << 33);
+        }
+        return;
+    }
+    uint64_t o[kWPL];
+    {
+        const ulonglong2* src =
+            reinterpret_cast<const ulonglong2*>(w.U + uint64_t(s) * w.NG * kGW + xb);
+        const ulonglong2 a = src[0], b = src[1];
+        o[0] = a.x;
+        o[1] = a.y;
+        o[2] = b.x;
+        o[3] = b.y;
+    }
+    const LocalScan L = local_scan(x0, x1, lane, o);
     uint32_t J = P.nh + (lane ? hf : 0u) + L.eh;  // heads before xb
     uint32_t Lc = P.nl + L.el;                    // literals before xb
     uint32_t hp, hcls, lg;
