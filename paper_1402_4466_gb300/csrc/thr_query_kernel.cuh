@@ -248,6 +248,51 @@ struct CsaCount {
 // policy (carry-save bit slices, or ScanCount counters).  kPos: mixed inputs
 // go through the position-major decode (ones counting; the host never sets
 // zmode for these kernels), literal runs through the grouped one.
+// The largest number of inputs with a non-zero word at one position of the
+// subtile: a literal run counts at every position, a mixed input where its
+// literal or ones-fill mask is set (32 inputs' masks bit-transposed across
+// the warp per row, then counted).  Records as the classification left
+// them (literal runs first and mixed inputs from the back with kPos).
+template <bool kPos>
+__device__ __forceinline__ uint32_t max_position_count(const PassAParams& p, const WarpSmem& ws,
+                                                       uint32_t nrec, uint32_t nrun,
+                                                       uint32_t nmix, uint32_t lane) {
+    uint32_t c[kRows] = {0, 0, 0, 0};
+    uint32_t runs = kPos ? nrun : 0u;
+    const uint32_t total = kPos ? nmix : nrec;
+    for (uint32_t m0 = 0; m0 < total; m0 += 32) {
+        const uint32_t j = m0 + lane;
+        uint32_t mk[kRows] = {0, 0, 0, 0};
+        bool run = false;
+        if (j < total) {
+            const uint4 rec = kPos ? ws.rec[kCH - 1 - j] : ws.rec[j];
+            if (!(rec.w >> 31)) {
+                run = true;
+            } else {
+                const uint4* m = reinterpret_cast<const uint4*>(
+                    p.masks + ((uint64_t(rec.y) << 32) | rec.x));
+                const uint4 lm = __ldg(m);
+                mk[0] = lm.x;
+                mk[1] = lm.y;
+                mk[2] = lm.z;
+                mk[3] = lm.w;
+                if ((rec.w >> 30) & 1u) {
+                    const uint4 om = __ldg(m + 2);
+                    mk[0] |= om.x;
+                    mk[1] |= om.y;
+                    mk[2] |= om.z;
+                    mk[3] |= om.w;
+                }
+            }
+        }
+        if (!kPos) runs += __popc(__ballot_sync(~0u, run));
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) c[r] += __popc(transpose32(mk[r], lane));
+    }
+    const uint32_t m = max(max(c[0], c[1]), max(c[2], c[3])) + runs;
+    return __reduce_max_sync(~0u, m);
+}
+
 // Counting part of a subtile's result: classify the query's inputs over the
 // subtile, count k (ones fills) and d (inputs with literals) and add the
 // active inputs into `count`.  kPart: the inputs are one part of a query
@@ -326,6 +371,14 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
             if (!kPart && (int64_t(q.Tmax()) <= int64_t(k_ones) ||
                            int64_t(q.T()) - int64_t(k_ones) > int64_t(d_act)))
                 break;
+            // finer: no word of the subtile is non-zero in T' inputs, so no
+            // row reaches T' (checked when T' is a fair share of d)
+            const int64_t tp = int64_t(q.T()) - int64_t(k_ones);
+            if (!kPart && tp >= 4 && 4 * tp >= int64_t(d_act) &&
+                int64_t(max_position_count<kPos>(p, ws, nrec, nrun, nmix, lane)) < tp) {
+                d_act = 0;  // finish: T' > d, every row zero
+                break;
+            }
         } else if (kPart) {
             d_act += nrec;
         }
