@@ -86,8 +86,10 @@ class Oracle:
                                       u64p, u64, u64p]
         lib.orc_threshold_words.argtypes = [u64p, u64p, u32, u64, u32p, u32,
                                             u32, u64p]
+        lib.orc_symmetric.argtypes = [u64p, u64p, u32, u64, u32p, u32, u32, u32,
+                                      ctypes.c_int, u64p, u64, u64p]
         for f in (lib.orc_encode, lib.orc_decode, lib.orc_validate,
-                  lib.orc_threshold, lib.orc_threshold_words):
+                  lib.orc_threshold, lib.orc_threshold_words, lib.orc_symmetric):
             f.restype = ctypes.c_int
         self.c = lib
 
@@ -133,6 +135,23 @@ class Oracle:
                                   ctypes.byref(n))
         if rc != OK:
             raise OracleError(rc, "threshold")
+        return out[: n.value].copy()
+
+    def symmetric(self, words, offsets, r: int, ids, lo: int, hi: int,
+                  odd: bool = False) -> np.ndarray:
+        """Canonical stream of the rows whose count c over ids satisfies
+        lo <= c <= hi (or, with odd, whose c is odd)."""
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        cap = nwords(r) + 1
+        out = np.empty(cap, dtype=np.uint64)
+        n = ctypes.c_uint64(0)
+        rc = self.c.orc_symmetric(_p64(words), _p64(offsets), len(offsets) - 1, int(r),
+                                  _p32(ids), ids.size, int(lo), int(hi), 1 if odd else 0,
+                                  _p64(out), cap, ctypes.byref(n))
+        if rc != OK:
+            raise OracleError(rc, "symmetric")
         return out[: n.value].copy()
 
     def threshold_words(self, words, offsets, r: int, ids, T: int) -> np.ndarray:
@@ -203,3 +222,6 @@ class Index:
     def threshold_words(self, ids, T: int) -> np.ndarray:
         return self._o().threshold_words(self.words, self.offsets, self.r,
                                          ids, T)
+
+    def symmetric(self, ids, lo: int, hi: int, odd: bool = False) -> np.ndarray:
+        return self._o().symmetric(self.words, self.offsets, self.r, ids, lo, hi, odd)

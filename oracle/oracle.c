@@ -242,6 +242,50 @@ done:
  * The same query, returning the uncompressed result words (W of them) instead
  * of the encoded stream; used to diagnose mismatches row by row.
  */
+/* Symmetric functions of the counts (beyond thresholds, Sec. 3.3 and Sec. 5.3
+ * discuss them as Boolean functions of the input bits that depend only on
+ * how many are set): the rows whose count c over the multiset of ids
+ * satisfies lo <= c <= hi, or, with odd != 0, whose c is odd (the XOR of the
+ * inputs).  The same ScanCount as orc_threshold, a different final test. */
+int orc_symmetric(const uint64_t *streams, const uint64_t *offsets,
+                  uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
+                  uint32_t n, uint32_t lo, uint32_t hi, int odd, uint64_t *out,
+                  uint64_t cap, uint64_t *out_len)
+{
+    uint64_t W = orc_nwords(r);
+    uint32_t *count = NULL;
+    uint64_t *rows = NULL, *words = NULL;
+    int rc = ORC_OK;
+    if (out_len == NULL || (n > 0 && ids == NULL) || offsets == NULL)
+        return ORC_E_INVAL;
+    for (uint32_t q = 0; q < n; q++)
+        if (ids[q] >= nbitmaps) return ORC_E_INVAL;
+    count = (uint32_t *)calloc(r > 0 ? r : 1, sizeof(uint32_t));
+    rows = (uint64_t *)malloc((r > 0 ? r : 1) * sizeof(uint64_t));
+    words = (uint64_t *)calloc(W > 0 ? W : 1, sizeof(uint64_t));
+    if (!count || !rows || !words) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    for (uint32_t q = 0; q < n; q++) {
+        uint64_t b = ids[q], nr = 0;
+        rc = orc_decode(streams + offsets[b], offsets[b + 1] - offsets[b], r,
+                        rows, r, &nr);
+        if (rc != ORC_OK) goto done;
+        for (uint64_t k = 0; k < nr; k++) count[rows[k]]++;
+    }
+    for (uint64_t x = 0; x < r; x++) {
+        const int keep = odd ? (int)(count[x] & 1u) : (count[x] >= lo && count[x] <= hi);
+        if (keep) words[x / 64] |= 1ull << (x % 64);
+    }
+    rc = orc_encode(words, W, r, out, cap, out_len);
+done:
+    free(count);
+    free(rows);
+    free(words);
+    return rc;
+}
+
 int orc_threshold_words(const uint64_t *streams, const uint64_t *offsets,
                         uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
                         uint32_t n, uint32_t T, uint64_t *words)
