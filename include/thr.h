@@ -140,6 +140,23 @@ thr_status thr_query(const thr_index *idx, const uint32_t *ids, uint32_t n,
                      uint64_t *out_len, uint32_t flags, void *cuda_stream);
 
 /*
+ * Symmetric-function query: the rows whose count c over the bitmaps
+ * ids[0..n) (duplicates counted with multiplicity) satisfies lo <= c <= hi,
+ * or, with THR_SYM_ODD in flags, whose c is odd (the XOR of the inputs; lo
+ * and hi are then ignored).  The threshold query is the range [T, n]; "at
+ * most T" is [0, T] and "exactly k" is [k, k].  Threshold functions are the
+ * symmetric Boolean functions the paper studies (Sec. 3.3); these are the
+ * other symmetric functions of the same counts.  The carry-save counters
+ * of thr_query are reused; only the final compare and the pruning differ
+ * (a subtile is zero when [k, k + d] misses [lo, hi] and ones when it lies
+ * inside).  Other arguments, output and errors as thr_query.
+ */
+#define THR_SYM_ODD 0x4000u
+thr_status thr_query_sym(const thr_index *idx, const uint32_t *ids, uint32_t n, uint32_t lo,
+                         uint32_t hi, uint64_t *out, uint64_t cap, uint64_t *out_len,
+                         uint32_t flags, void *cuda_stream);
+
+/*
  * Batch of nq threshold queries (Sec. 2) over one index.
  *   id_off    host array of nq + 1 offsets into ids; query q uses
  *             ids[id_off[q] .. id_off[q+1])

@@ -27,6 +27,7 @@ THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_PROFILE = 0x100
 THR_NO_GRAPH = 0x1000
 THR_NO_SHARE = 0x2000
+THR_SYM_ODD = 0x4000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 THR_VARIANT_SPLIT = 0x600
 
@@ -42,7 +43,7 @@ ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_stati
                "thr_selector_predict", "thr_selector_gradients", "thr_query_features",
                "thr_index_set_selector", "thr_server_create", "thr_server_submit",
                "thr_server_wait", "thr_server_stats", "thr_server_free", "thr_rle_encode_rows",
-               "thr_rle_slice", "thr_rle_stitch",
+               "thr_rle_slice", "thr_rle_stitch", "thr_query_sym",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -81,6 +82,7 @@ def load():
             lib.thr_rle_validate.argtypes = [vp, u64, u64]
             lib.thr_rle_encode_rows.argtypes = [vp, u64, u64, vp, u64, u64p]
             lib.thr_rle_slice.argtypes = [vp, u64, u64, u64, u64, vp, u64, u64p]
+            lib.thr_query_sym.argtypes = [vp, vp, u32, u32, u32, vp, u64, u64p, u32, vp]
             lib.thr_rle_stitch.argtypes = [vp, vp, vp, u32, vp, u64, u64p]
             lib.thr_last_error.argtypes = []
             lib.thr_last_error.restype = ctypes.c_char_p
@@ -118,7 +120,7 @@ def load():
                       "thr_selector_gradients", "thr_query_features", "thr_index_set_selector",
                       "thr_server_create", "thr_server_submit", "thr_server_wait",
                       "thr_server_stats", "thr_rle_encode_rows", "thr_rle_slice",
-                      "thr_rle_stitch"):
+                      "thr_rle_stitch", "thr_query_sym"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -230,6 +232,33 @@ def thr_query(idx: Index, ids, T: int, out=None, flags: int = 0, stream=None,
     if st == THR_E_NOSPACE:
         raise ThrError(st, "thr_query", f"needs {n.value} words")
     _check(st, "thr_query")
+    return n.value
+
+
+def thr_query_sym(idx: Index, ids, lo: int = 0, hi: int | None = None, odd: bool = False,
+                  out=None, stream=None):
+    """Rows whose count over ids lies in [lo, hi] (hi=None: n), or with
+    odd=True whose count is odd.  Returns the stream (out=None) or fills a
+    device tensor / host array and returns the number of words."""
+    lib = load()
+    ids = _u32(ids)
+    hi = ids.size if hi is None else int(hi)
+    flags = THR_SYM_ODD if odd else 0
+    n = ctypes.c_uint64(0)
+    if out is None:
+        buf = np.empty(idx.nwords + 1, dtype=np.uint64)
+        _check(lib.thr_query_sym(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                                 ids.size, int(lo), hi, ctypes.c_void_p(buf.ctypes.data),
+                                 buf.size, ctypes.byref(n), flags,
+                                 ctypes.c_void_p(_stream(stream))), "thr_query_sym")
+        return buf[: n.value].copy()
+    if getattr(out, "is_cuda", False):
+        flags |= THR_OUT_DEVICE
+    size = out.numel() if hasattr(out, "numel") else out.size
+    _check(lib.thr_query_sym(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                             ids.size, int(lo), hi, ctypes.c_void_p(_ptr(out)), int(size),
+                             ctypes.byref(n), flags, ctypes.c_void_p(_stream(stream))),
+           "thr_query_sym")
     return n.value
 
 

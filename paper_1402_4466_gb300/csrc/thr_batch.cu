@@ -137,7 +137,7 @@ void form_groups(const BatchInput& in, uint32_t q0, uint32_t Q, std::vector<QDes
     std::vector<std::vector<uint32_t>> sorted(Q);
     for (uint32_t s = 0; s < Q; ++s) {
         const uint32_t q = q0 + s;
-        if (class_family(qcls[q]) != 0) continue;
+        if (class_family(qcls[q]) != 0 || qd[q].sym != kSymThreshold) continue;
         sorted[s].assign(in.ids + in.id_off[q], in.ids + in.id_off[q + 1]);
         std::sort(sorted[s].begin(), sorted[s].end());
         uint64_t h = fnv(14695981039346656037ull, sorted[s].size());
@@ -223,8 +223,25 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         const uint32_t n = in.id_off[q + 1] - in.id_off[q];
         int cls = 0;
         uint32_t z = 0;
-        resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls, &z);
-        qd[q] = QDesc{in.id_off[q], n, in.T[q], z, in.T[q], in.T[q]};
+        const uint32_t sym = in.sym ? in.sym[q] : kSymThreshold;
+        const uint32_t hi = (in.hi && sym == kSymRange) ? in.hi[q] : 0u;
+        if (sym == kSymThreshold) {
+            resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls, &z);
+        } else {  // ranges and parity: carry-save counting ones, 2^S > min(hi, n) + 1
+            const uint64_t top = sym == kSymRange ? std::min<uint64_t>(hi, n) + 1 : 1;
+            int need = 0;
+            for (uint64_t v = top; v; v >>= 1) ++need;
+            int cnt = 0;
+            const KernelEntry* tab = kernel_table(&cnt);
+            cls = cnt - 1;
+            for (int w = 0; w < cnt; ++w)
+                if (tab[w].S >= need) {
+                    cls = w;
+                    break;
+                }
+            z = 0;
+        }
+        qd[q] = QDesc{in.id_off[q], n, in.T[q], z, in.T[q], in.T[q], hi, sym};
         qcls[q] = uint8_t(cls);
     }
     // groups of queries over the same id multiset (grouped carry-save, same

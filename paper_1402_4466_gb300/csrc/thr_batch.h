@@ -20,6 +20,8 @@ struct BatchInput {
     const uint32_t* ids;
     const uint32_t* T;
     const uint8_t* variant;  // counting variant per query (kVar*), or null (kVarCsa)
+    const uint8_t* sym = nullptr;  // kSym* per query, or null (thresholds)
+    const uint32_t* hi = nullptr;  // range upper bounds (kSymRange queries)
 };
 
 struct BatchOptions {

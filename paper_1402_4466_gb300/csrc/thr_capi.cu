@@ -523,6 +523,46 @@ thr_status thr_autotune(const thr_index* idx, uint32_t nq, const uint32_t* id_of
                     !(flags & THR_NO_SHARE));
 }
 
+thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, uint32_t lo,
+                         uint32_t hi, uint64_t* out, uint64_t cap, uint64_t* out_len,
+                         uint32_t flags, void* cuda_stream) {
+    if (!idx || !ids || !out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null argument");
+    if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
+    if (flags & ~(THR_OUT_DEVICE | THR_SYM_ODD)) return fail(THR_E_INVAL, "unknown flags");
+    for (uint32_t i = 0; i < n; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    const uint8_t sym = (flags & THR_SYM_ODD) ? uint8_t(kSymOdd) : uint8_t(kSymRange);
+    const uint32_t id_off[2] = {0, n};
+    const uint8_t var = uint8_t(kVarCsa);
+    BatchInput in{1, id_off, ids, &lo, &var, &sym, &hi};
+    BatchOptions opt;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint64_t off = 0, total = 0;
+    if (flags & THR_OUT_DEVICE) {
+        if (cap > 0 && !is_device_ptr(out))
+            return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+        thr_status s = run_batch(idx, in, out, cap, &off, out_len, &total, st, opt, nullptr);
+        if (s != THR_OK) return s;
+        if (*out_len > cap)
+            return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)*out_len);
+        return THR_OK;
+    }
+    const uint64_t dcap = std::min<uint64_t>(cap, uint64_t(idx->W) + 1);
+    Scratch scr(st);
+    uint64_t* dbuf = nullptr;
+    CK(scr.alloc((void**)&dbuf, sizeof(uint64_t) * std::max<uint64_t>(dcap, 1)),
+       "scratch (output)");
+    thr_status s = run_batch(idx, in, dbuf, dcap, &off, out_len, &total, st, opt, nullptr);
+    if (s != THR_OK) return s;
+    if (*out_len > cap)
+        return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)*out_len);
+    CK(cudaMemcpyAsync(out, dbuf, sizeof(uint64_t) * *out_len, cudaMemcpyDeviceToHost, st),
+       "copy result");
+    CK(cudaStreamSynchronize(st), "copy result");
+    return THR_OK;
+}
+
 thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint64_t* pool,
                            uint64_t pool_cap, uint64_t* out_off, uint64_t* out_len,

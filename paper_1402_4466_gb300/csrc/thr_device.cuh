@@ -91,10 +91,15 @@ constexpr int kAggWords = 8;
 struct QDesc {
     uint32_t ids_off;  // first id in the batch's id array
     uint32_t n;
-    uint32_t T;
+    uint32_t T;        // threshold, or the lower bound of a range
     uint32_t zmode;
     uint32_t Tlo, Thi;
+    uint32_t hi;       // range queries: the upper bound
+    uint32_t sym;      // kSymThreshold, kSymRange or kSymOdd
 };
+// What a query computes from the count c of a row: c >= T (threshold),
+// T <= c <= hi (range: at most, exactly, between), c odd (the XOR).
+constexpr uint32_t kSymThreshold = 0, kSymRange = 1, kSymOdd = 2;
 
 // Pass A of one launch: the queries (slots of the chunk) in list[0..nlist),
 // one work item per (query, subtile), query-major (order 0) or subtile-major

@@ -110,7 +110,7 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     int cls = 0;
     uint32_t zmode = 0;
     choose_class(n, T, &cls, &zmode);
-    const QDesc qd{0, n, T, zmode, T, T};
+    const QDesc qd{0, n, T, zmode, T, T, 0u, kSymThreshold};
     const uint2 grp1 = make_uint2(0, 1);
     const uint32_t slot0 = 0;
     if ((e = cudaMemcpyAsync(blk, &qd, sizeof qd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||

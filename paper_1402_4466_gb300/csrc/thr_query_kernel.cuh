@@ -27,6 +27,7 @@ struct WarpSmem {
     uint32_t ids[kCH];             //   and the ids, when n <= kCH
     uint32_t qn, qT, qz, qoff;     // the current query: n, T, zmode, first id
     uint32_t qTx;                  //   largest threshold of its group (qT: the least)
+    uint32_t qhi, qsym;            //   range bound and kind (QDesc)
 };
 
 struct CtaSmem {
@@ -42,6 +43,20 @@ struct QView {
     __device__ __forceinline__ uint32_t n() const { return w.qn; }
     __device__ __forceinline__ uint32_t T() const { return w.qT; }
     __device__ __forceinline__ uint32_t Tmax() const { return w.qTx; }
+    __device__ __forceinline__ uint32_t hi() const { return w.qhi; }
+    __device__ __forceinline__ uint32_t sym() const { return w.qsym; }
+    // Is the subtile decided by k ones fills and d inputs with literals
+    // (every row's count lies in [k, k + d]): all ones or all zeros, for
+    // every threshold of a group?
+    __device__ __forceinline__ bool decided(uint32_t k, uint32_t d) const {
+        const uint32_t s = w.qsym;
+        const int64_t lo = int64_t(w.qT) - int64_t(k);
+        if (s == kSymOdd) return d == 0;
+        if (s == kSymRange)
+            return int64_t(w.qhi) < int64_t(k) || lo > int64_t(d) ||
+                   (lo <= 0 && int64_t(k) + int64_t(d) <= int64_t(w.qhi));
+        return int64_t(w.qTx) <= int64_t(k) || lo > int64_t(d);
+    }
     __device__ __forceinline__ uint32_t zmode() const { return w.qz; }
     __device__ __forceinline__ const uint32_t* ids() const { return all_ids + w.qoff; }
     __device__ __forceinline__ bool cached() const { return w.qn <= uint32_t(kCH); }
@@ -216,7 +231,14 @@ static_assert(kGroup == 2 || kGroup == 4, "inputs are added in fours or twos");
 
 template <int S>
 struct CsaCount {
+    static constexpr bool kSymmetric = true;  // range and parity tests
     Counters<S> cnt;
+    // the lowest slice is the parity of the count (never saturated)
+    __device__ __forceinline__ void parity(uint64_t (&o)[kRows], uint32_t flip) const {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+            o[r] = (uint64_t(cnt.c[0][2 * r + 1] ^ flip) << 32) | (cnt.c[0][2 * r] ^ flip);
+    }
     __device__ __forceinline__ void begin() { cnt.clear(); }
     __device__ __forceinline__ void add(const uint64_t (&v)[kGroup][kRows], uint32_t) {
 #pragma unroll
@@ -319,8 +341,7 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
             k_ones += __popc(__ballot_sync(~0u, cls == 1));
             d_act += __popc(__ballot_sync(~0u, cls >= 2));
         }
-        pruned = int64_t(q.Tmax()) <= int64_t(k_ones) ||
-                 int64_t(q.T()) - int64_t(k_ones) > int64_t(d_act);
+        pruned = q.decided(k_ones, d_act);
     }
     for (uint32_t c0 = 0; c0 < q.n() && !pruned; c0 += kCH) {
         const uint32_t cn = min(uint32_t(kCH), q.n() - c0);
@@ -368,13 +389,11 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
         if (one_chunk) {  // run-aware pruning (Sec. 6.4 cases 1 and 2)
             d_act = nrec;
             // decided for every threshold of the group: all ones or all zeros
-            if (!kPart && (int64_t(q.Tmax()) <= int64_t(k_ones) ||
-                           int64_t(q.T()) - int64_t(k_ones) > int64_t(d_act)))
-                break;
+            if (!kPart && q.decided(k_ones, d_act)) break;
             // finer: no word of the subtile is non-zero in T' inputs, so no
             // row reaches T' (checked when T' is a fair share of d)
             const int64_t tp = int64_t(q.T()) - int64_t(k_ones);
-            if (!kPart && tp >= 4 && 4 * tp >= int64_t(d_act) &&
+            if (!kPart && q.sym() != kSymOdd && tp >= 4 && 4 * tp >= int64_t(d_act) &&
                 int64_t(max_position_count<kPos>(p, ws, nrec, nrun, nmix, lane)) < tp) {
                 d_act = 0;  // finish: T' > d, every row zero
                 break;
@@ -418,20 +437,48 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
 
 // Compare with T' = T - k (or count the zeros against d - T' + 1) and mask
 // the words past W: the subtile's result words (row r of the lane in o[r]).
+// Range queries test lo' <= c' <= hi' on the active count c' (two compares),
+// odd-count queries take the lowest counter slice and the parity of k.
 template <class Count>
 __device__ __forceinline__ void finish_subtile(const PassAParams& p, uint32_t T, uint32_t zmode,
-                                               uint32_t k_ones, uint32_t d_act, uint32_t x0,
-                                               uint32_t lane, Count& count,
-                                               uint64_t (&o)[kRows]) {
+                                               uint32_t hi, uint32_t sym, uint32_t k_ones,
+                                               uint32_t d_act, uint32_t x0, uint32_t lane,
+                                               Count& count, uint64_t (&o)[kRows]) {
 #pragma unroll
     for (int r = 0; r < kRows; ++r) o[r] = 0;
     const int64_t Tp = int64_t(T) - int64_t(k_ones);
-    if (Tp <= 0) {
+    if constexpr (Count::kSymmetric) {
+        if (sym == kSymOdd) {
+            count.parity(o, (k_ones & 1u) ? ~0u : 0u);
+        } else if (sym == kSymRange) {
+            const int64_t Hp = int64_t(hi) - int64_t(k_ones);
+            if (Hp >= 0 && Tp <= int64_t(d_act)) {
+                uint64_t a[kRows], b[kRows];
+                if (Tp <= 0) {
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) o[r] = ~0ull;
-    } else if (Tp <= int64_t(d_act)) {
-        const uint32_t thr = zmode ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
-        count.finish(thr, zmode ? ~0u : 0u, o);
+                    for (int r = 0; r < kRows; ++r) a[r] = ~0ull;
+                } else {
+                    count.finish(uint32_t(Tp), 0u, a);
+                }
+                if (Hp + 1 > int64_t(d_act)) {
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) b[r] = 0;
+                } else {
+                    count.finish(uint32_t(Hp + 1), 0u, b);
+                }
+#pragma unroll
+                for (int r = 0; r < kRows; ++r) o[r] = a[r] & ~b[r];
+            }
+        }
+    }
+    if (sym == kSymThreshold) {
+        if (Tp <= 0) {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) o[r] = ~0ull;
+        } else if (Tp <= int64_t(d_act)) {
+            const uint32_t thr = zmode ? uint32_t(int64_t(d_act) - Tp + 1) : uint32_t(Tp);
+            count.finish(thr, zmode ? ~0u : 0u, o);
+        }
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -440,7 +487,6 @@ __device__ __forceinline__ void finish_subtile(const PassAParams& p, uint32_t T,
         else if (x == p.W - 1 && p.ragged) o[r] &= (1ull << p.ragged) - 1;
     }
 }
-
 
 // Canonical re-encoding, part 1 (per subtile, by its warp).  o[q] is word
 // xb + q, xb = x0 + 4 lane.  Word classes (0 zero, 1 ones, 2 literal) give
@@ -534,7 +580,8 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
 // cached in the warp's shared memory when n <= kCH.
 __device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, uint32_t ids_off,
                                            uint32_t n, uint32_t T, uint32_t zmode,
-                                           uint32_t Tmax, uint32_t lane) {
+                                           uint32_t Tmax, uint32_t hi, uint32_t sym,
+                                           uint32_t lane) {
     __syncwarp();
     if (lane == 0) {
         ws.qn = n;
@@ -542,6 +589,8 @@ __device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, u
         ws.qz = zmode;
         ws.qoff = ids_off;
         ws.qTx = Tmax;
+        ws.qhi = hi;
+        ws.qsym = sym;
     }
     if (n <= uint32_t(kCH)) {
         for (uint32_t i = lane; i < n; i += 32) {
@@ -628,7 +677,7 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
         const uint32_t s = __ldg(p.list + li);
         if (s != cur) {  // a new query: its parameters, and its ids when they fit
             const QDesc d = p.qd[s];
-            load_query(p, ws, d.ids_off, d.n, d.Tlo, d.zmode, d.Thi, lane);
+            load_query(p, ws, d.ids_off, d.n, d.Tlo, d.zmode, d.Thi, d.hi, d.sym, lane);
             grp = p.grp[s];
             cur = s;
         }
@@ -638,12 +687,14 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
         uint32_t k_ones = 0, d_act = 0;
         count_subtile<Count, kPos, false>(p, q, x0, x1, lane, ws, count, k_ones, d_act);
         if (grp.y <= 1) {
-            finish_subtile(p, q.T(), q.zmode(), k_ones, d_act, x0, lane, count, orow);
+            finish_subtile(p, q.T(), q.zmode(), q.hi(), q.sym(), k_ones, d_act, x0, lane, count,
+                           orow);
             store_subtile(p, ws, cur, g, x0, x1, lane, orow);
         } else {  // one count, every member's threshold (ones counted)
             for (uint32_t i = 0; i < grp.y; ++i) {
                 const uint32_t m = __ldg(p.memb + grp.x + i);
-                finish_subtile(p, p.qd[m].T, 0u, k_ones, d_act, x0, lane, count, orow);
+                finish_subtile(p, p.qd[m].T, 0u, 0u, kSymThreshold, k_ones, d_act, x0, lane,
+                               count, orow);
                 store_subtile(p, ws, m, g, x0, x1, lane, orow);
             }
         }
@@ -694,7 +745,7 @@ __global__ void __launch_bounds__(kNT, 4) k_threshold_split(const PassAParams p)
             const QDesc d = p.qd[s];
             const uint32_t a = uint32_t(uint64_t(d.n) * wid / kNW);
             const uint32_t b = uint32_t(uint64_t(d.n) * (wid + 1) / kNW);
-            load_query(p, ws, d.ids_off + a, b - a, d.T, d.zmode, d.T, lane);
+            load_query(p, ws, d.ids_off + a, b - a, d.T, d.zmode, d.T, d.hi, d.sym, lane);
             T = d.T;
             zmode = d.zmode;
             cur = s;
@@ -725,7 +776,7 @@ __global__ void __launch_bounds__(kNT, 4) k_threshold_split(const PassAParams p)
             if (live)
                 for (int w = 1; w < kNW; ++w) count.cnt.add_from(part + (w - 1) * kSliceWords, lane);
             uint64_t orow[kRows];
-            finish_subtile(p, T, zmode, K, D, x0, lane, count, orow);
+            finish_subtile(p, T, zmode, 0u, kSymThreshold, K, D, x0, lane, count, orow);
             store_subtile(p, ws, cur, g, x0, x1, lane, orow);
         }
         __syncthreads();

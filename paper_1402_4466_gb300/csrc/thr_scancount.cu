@@ -18,6 +18,7 @@ constexpr uint32_t kRowsPerWord = 64;
 constexpr uint32_t kCounterBytes = kRowsPerWord * kGW;  // per warp
 
 struct ScanCount {
+    static constexpr bool kSymmetric = false;  // thresholds only
     unsigned char* cnt;
     uint32_t lane;
     uint32_t cf[kRows];  // ones-fill words seen at the lane's word of row r

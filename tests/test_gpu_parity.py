@@ -304,3 +304,48 @@ def test_split_many_criteria_full_size(many_criteria_full):
     p = Pair(words, r)
     for T in (*synth.MANY_TS, 1, 64):
         p.check(list(range(synth.MANY_N)), T, SPLIT)
+
+
+# ---- symmetric functions of the counts: ranges and odd counts
+
+def _check_sym(p, ids, lo, hi, odd=False):
+    got = thr.thr_query_sym(p.g, ids, lo, hi, odd=odd)
+    want = p.o.symmetric(ids, lo, hi, odd)
+    assert np.array_equal(got, want), f"ids n={len(ids)} lo={lo} hi={hi} odd={odd}"
+
+
+def test_symmetric_random_tiny_every_range():
+    rng = np.random.default_rng(505)
+    for _ in range(12):
+        n = int(rng.integers(1, 9))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        ids = rng.integers(0, n, int(rng.integers(1, 2 * n + 1))).tolist()
+        for lo in range(0, len(ids) + 2):
+            for hi in range(lo, len(ids) + 2):
+                _check_sym(p, ids, lo, hi)
+        _check_sym(p, ids, 0, 0, odd=True)
+
+
+def test_symmetric_several_tiles_and_chunks():
+    r = (1 << 18) + 77
+    words, _ = synth.many_criteria(17, 30, r)
+    p = Pair(words, r)
+    ids = list(range(30))
+    for lo, hi in ((0, 0), (0, 2), (1, 1), (2, 5), (3, 30), (10, 12), (29, 29), (31, 40)):
+        _check_sym(p, ids, lo, hi)
+    _check_sym(p, ids, 0, 0, odd=True)
+    rng = np.random.default_rng(18)
+    ids = rng.integers(0, 30, size=300).tolist()  # n > 128: record chunks
+    for lo, hi in ((0, 3), (5, 20), (40, 300)):
+        _check_sym(p, ids, lo, hi)
+    _check_sym(p, ids, 0, 0, odd=True)
+
+
+def test_symmetric_many_criteria_full_size(many_criteria_full):
+    words, r = many_criteria_full
+    p = Pair(words, r)
+    ids = list(range(synth.MANY_N))
+    for lo, hi in ((0, 1), (1, 1), (2, 4), (5, 64)):
+        _check_sym(p, ids, lo, hi)
+    _check_sym(p, ids, 0, 0, odd=True)
