@@ -300,6 +300,17 @@ def run_ours(args):
             ts = [plain_query(T, vflag)[1] for _ in range(max(args.steps, 3))]
             per_t[str(T)] = round(statistics.median(ts), 5)
         variant_ms[vname] = per_t
+    # symmetric functions of the same counts (at most 1, exactly 2, 2..4, odd)
+    sym_ms = {}
+    for name, lo, hi, odd in (("at_most_1", 0, 1, False), ("exactly_2", 2, 2, False),
+                              ("between_2_4", 2, 4, False), ("odd", 0, 0, True)):
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            flushed()
+            thr.thr_query_sym(idx, ids, lo, hi, odd=odd, out=dout, stream=stream,
+                              flags=thr.THR_PROFILE)
+            ts.append(thr.thr_last_kernel_ms())
+        sym_ms[name] = round(statistics.median(ts), 5)
     clk = clocks.stop()
 
     # end to end through the C ABI: host ids in, host result pool out (the
@@ -378,6 +389,7 @@ def run_ours(args):
                     "autotune_ms": [round(t, 4) for t in batch_tune_ms],
                     "single_query_autotune_ms": [round(t, 4) for t in single_tune_ms]},
         "pass_a_ms_by_variant": variant_ms,
+        "pass_a_ms_symmetric": sym_ms,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

@@ -236,14 +236,14 @@ def thr_query(idx: Index, ids, T: int, out=None, flags: int = 0, stream=None,
 
 
 def thr_query_sym(idx: Index, ids, lo: int = 0, hi: int | None = None, odd: bool = False,
-                  out=None, stream=None):
+                  out=None, stream=None, flags: int = 0):
     """Rows whose count over ids lies in [lo, hi] (hi=None: n), or with
     odd=True whose count is odd.  Returns the stream (out=None) or fills a
     device tensor / host array and returns the number of words."""
     lib = load()
     ids = _u32(ids)
     hi = ids.size if hi is None else int(hi)
-    flags = THR_SYM_ODD if odd else 0
+    flags |= THR_SYM_ODD if odd else 0
     n = ctypes.c_uint64(0)
     if out is None:
         buf = np.empty(idx.nwords + 1, dtype=np.uint64)

@@ -528,7 +528,8 @@ thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, 
                          uint32_t flags, void* cuda_stream) {
     if (!idx || !ids || !out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null argument");
     if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
-    if (flags & ~(THR_OUT_DEVICE | THR_SYM_ODD)) return fail(THR_E_INVAL, "unknown flags");
+    if (flags & ~(THR_OUT_DEVICE | THR_SYM_ODD | THR_PROFILE))
+        return fail(THR_E_INVAL, "unknown flags");
     for (uint32_t i = 0; i < n; ++i)
         if (ids[i] >= idx->nbitmaps)
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
@@ -537,13 +538,16 @@ thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, 
     const uint8_t var = uint8_t(kVarCsa);
     BatchInput in{1, id_off, ids, &lo, &var, &sym, &hi};
     BatchOptions opt;
+    opt.profile = flags & THR_PROFILE;
+    BatchStats stats;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t off = 0, total = 0;
     if (flags & THR_OUT_DEVICE) {
         if (cap > 0 && !is_device_ptr(out))
             return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
-        thr_status s = run_batch(idx, in, out, cap, &off, out_len, &total, st, opt, nullptr);
+        thr_status s = run_batch(idx, in, out, cap, &off, out_len, &total, st, opt, &stats);
         if (s != THR_OK) return s;
+        if (opt.profile) g_kernel_ms = stats.pass_a_ms;
         if (*out_len > cap)
             return fail(THR_E_NOSPACE, "result needs %llu words", (unsigned long long)*out_len);
         return THR_OK;
