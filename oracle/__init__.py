@@ -16,6 +16,10 @@ Parity status: every function is pinned by ``tests/test_oracle_pins.py`` (the
 paper's worked examples, brute force on tiny inputs, independent Looped and
 BSTM implementations, closed-form invariants and hand-written format cases);
 ``tests/test_oracle_mutants.py`` shows that plausible mistakes fail them.
+The symmetric-function queries are pinned by ``tests/test_oracle_symmetric.py``
+and the opt-threshold query by ``tests/test_oracle_opt.py`` (brute force, the
+descending search of Sec. 5.2, the Looped route of Sec. 6.2, planted
+mistakes).
 """
 from __future__ import annotations
 
@@ -88,8 +92,11 @@ class Oracle:
                                             u32, u64p]
         lib.orc_symmetric.argtypes = [u64p, u64p, u32, u64, u32p, u32, u32, u32,
                                       ctypes.c_int, u64p, u64, u64p]
+        lib.orc_opt_threshold.argtypes = [u64p, u64p, u32, u64, u32p, u32, u64, u32p,
+                                          u64p, u64, u64p]
         for f in (lib.orc_encode, lib.orc_decode, lib.orc_validate,
-                  lib.orc_threshold, lib.orc_threshold_words, lib.orc_symmetric):
+                  lib.orc_threshold, lib.orc_threshold_words, lib.orc_symmetric,
+                  lib.orc_opt_threshold):
             f.restype = ctypes.c_int
         self.c = lib
 
@@ -153,6 +160,23 @@ class Oracle:
         if rc != OK:
             raise OracleError(rc, "symmetric")
         return out[: n.value].copy()
+
+    def opt_threshold(self, words, offsets, r: int, ids, K: int = 1):
+        """(T, stream): the largest T whose T-overlap result over ids holds at
+        least K rows (0 when none does), and that result."""
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        cap = nwords(r) + 1
+        out = np.empty(cap, dtype=np.uint64)
+        n = ctypes.c_uint64(0)
+        T = ctypes.c_uint32(0)
+        rc = self.c.orc_opt_threshold(_p64(words), _p64(offsets), len(offsets) - 1, int(r),
+                                      _p32(ids), ids.size, int(K), ctypes.byref(T), _p64(out),
+                                      cap, ctypes.byref(n))
+        if rc != OK:
+            raise OracleError(rc, "opt_threshold")
+        return int(T.value), out[: n.value].copy()
 
     def threshold_words(self, words, offsets, r: int, ids, T: int) -> np.ndarray:
         """Uncompressed result words of the same query."""
@@ -225,3 +249,6 @@ class Index:
 
     def symmetric(self, ids, lo: int, hi: int, odd: bool = False) -> np.ndarray:
         return self._o().symmetric(self.words, self.offsets, self.r, ids, lo, hi, odd)
+
+    def opt_threshold(self, ids, K: int = 1):
+        return self._o().opt_threshold(self.words, self.offsets, self.r, ids, K)

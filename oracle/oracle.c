@@ -286,6 +286,67 @@ done:
     return rc;
 }
 
+/* Opt-threshold query (Sec. 3.3, last paragraph; Sec. 5.1 derives it from
+ * ScanCount): T is not given; the answer is the largest T in [0, n] whose
+ * T-overlap result holds at least K rows (K = 1: the largest count any row
+ * reaches), and that result.  ScanCount's counters as in orc_threshold,
+ * then a histogram of the counts, whose suffix sums from n downwards give
+ * |result_T| for every T; the first T (from the top) with a suffix of at
+ * least K rows is the answer.  When no T qualifies (K > r) the answer is
+ * T = 0, every row.  *T_out receives T. */
+int orc_opt_threshold(const uint64_t *streams, const uint64_t *offsets,
+                      uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
+                      uint32_t n, uint64_t K, uint32_t *T_out, uint64_t *out,
+                      uint64_t cap, uint64_t *out_len)
+{
+    uint64_t W = orc_nwords(r);
+    uint32_t *count = NULL;
+    uint64_t *rows = NULL, *words = NULL, *hist = NULL;
+    int rc = ORC_OK;
+    if (out_len == NULL || T_out == NULL || (n > 0 && ids == NULL) || offsets == NULL || K == 0)
+        return ORC_E_INVAL;
+    for (uint32_t q = 0; q < n; q++)
+        if (ids[q] >= nbitmaps) return ORC_E_INVAL;
+    count = (uint32_t *)calloc(r > 0 ? r : 1, sizeof(uint32_t));
+    rows = (uint64_t *)malloc((r > 0 ? r : 1) * sizeof(uint64_t));
+    words = (uint64_t *)calloc(W > 0 ? W : 1, sizeof(uint64_t));
+    hist = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    if (!count || !rows || !words || !hist) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    for (uint32_t q = 0; q < n; q++) {
+        uint64_t b = ids[q], nr = 0;
+        rc = orc_decode(streams + offsets[b], offsets[b + 1] - offsets[b], r,
+                        rows, r, &nr);
+        if (rc != ORC_OK) goto done;
+        for (uint64_t k = 0; k < nr; k++) count[rows[k]]++;
+    }
+    /* hist[c] = rows whose count is exactly c */
+    for (uint64_t x = 0; x < r; x++) hist[count[x]]++;
+    {
+        uint32_t T = 0;
+        uint64_t atleast = 0; /* rows whose count is >= c */
+        for (uint32_t c = n; c >= 1; c--) {
+            atleast += hist[c];
+            if (atleast >= K) {
+                T = c;
+                break;
+            }
+        }
+        *T_out = T;
+        for (uint64_t x = 0; x < r; x++)
+            if (count[x] >= T) words[x / 64] |= 1ull << (x % 64);
+    }
+    rc = orc_encode(words, W, r, out, cap, out_len);
+done:
+    free(count);
+    free(rows);
+    free(words);
+    free(hist);
+    return rc;
+}
+
 int orc_threshold_words(const uint64_t *streams, const uint64_t *offsets,
                         uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
                         uint32_t n, uint32_t T, uint64_t *words)
