@@ -311,6 +311,21 @@ def run_ours(args):
                               flags=thr.THR_PROFILE)
             ts.append(thr.thr_last_kernel_ms())
         sym_ms[name] = round(statistics.median(ts), 5)
+    # opt-threshold (largest T with K rows): the profiling pass alone, and the
+    # whole call (profiling pass, histogram read, threshold query at T)
+    opt = {}
+    for K in (1, 1000):
+        prof, whole, Tk = [], [], 0
+        for _ in range(max(args.steps, 3)):
+            flushed()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            Tk, _ = thr.thr_query_opt(idx, ids, K, out=dout, stream=stream,
+                                      flags=thr.THR_PROFILE)
+            whole.append((time.perf_counter() - t1) * 1e3)
+            prof.append(thr.thr_last_kernel_ms())
+        opt[f"K={K}"] = {"T": int(Tk), "profile_ms": round(statistics.median(prof), 5),
+                         "call_ms": round(statistics.median(whole), 5)}
     clk = clocks.stop()
 
     # end to end through the C ABI: host ids in, host result pool out (the
@@ -390,6 +405,7 @@ def run_ours(args):
                     "single_query_autotune_ms": [round(t, 4) for t in single_tune_ms]},
         "pass_a_ms_by_variant": variant_ms,
         "pass_a_ms_symmetric": sym_ms,
+        "opt_threshold": opt,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

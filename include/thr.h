@@ -157,6 +157,41 @@ thr_status thr_query_sym(const thr_index *idx, const uint32_t *ids, uint32_t n, 
                          uint32_t flags, void *cuda_stream);
 
 /*
+ * Opt-threshold query (Sec. 3.3, last paragraph; Sec. 5.1 and Sec. 6.2 give
+ * it for ScanCount and Looped): T is not given.  *T_out receives
+ *   T* = the largest T in 0..n whose T-overlap result over ids[0..n) holds
+ *        at least K rows (K = 1: the largest count any row reaches),
+ *        or 0 when no T does (only when K > r: the T = 0 result is every row),
+ * and out receives that result, as thr_query(ids, n, T*) would write it (for
+ * K = 1 exactly the rows whose count is T*).  The generalisation to K rows
+ * is the one Sec. 3.3 suggests; ties at T* are all kept (it is not a top-K
+ * list).  Two passes on cuda_stream: a profiling pass of the carry-save
+ * counters (a histogram of the counts at or above a rising lower bound on
+ * T*, skipping subtiles that cannot reach it), a device->host read of the
+ * histogram, then the threshold query at T*.
+ *   K      >= 1 (THR_E_INVAL otherwise)
+ *   n      1..65535
+ *   flags  THR_OUT_DEVICE, THR_PROFILE (thr_last_kernel_ms then returns the
+ *          profiling pass's time), one THR_VARIANT_* value for the second pass
+ * Other arguments, output and errors as thr_query; *T_out is set whenever
+ * the profiling pass ran, also when the result does not fit (THR_E_NOSPACE).
+ */
+thr_status thr_query_opt(const thr_index *idx, const uint32_t *ids, uint32_t n, uint64_t K,
+                         uint32_t *T_out, uint64_t *out, uint64_t cap, uint64_t *out_len,
+                         uint32_t flags, void *cuda_stream);
+
+/*
+ * nq opt-threshold queries (as thr_query_opt) in one profiling launch per
+ * counter width and one thr_query_batch: K and T_out have nq entries; the
+ * other arguments, flags and output as thr_query_batch.  Results equal nq
+ * calls of thr_query_opt.
+ */
+thr_status thr_query_opt_batch(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
+                               const uint32_t *ids, const uint64_t *K, uint32_t *T_out,
+                               uint64_t *pool, uint64_t pool_cap, uint64_t *out_off,
+                               uint64_t *out_len, uint32_t flags, void *cuda_stream);
+
+/*
  * Batch of nq threshold queries (Sec. 2) over one index.
  *   id_off    host array of nq + 1 offsets into ids; query q uses
  *             ids[id_off[q] .. id_off[q+1])

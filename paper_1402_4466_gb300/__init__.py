@@ -43,7 +43,8 @@ ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_stati
                "thr_selector_predict", "thr_selector_gradients", "thr_query_features",
                "thr_index_set_selector", "thr_server_create", "thr_server_submit",
                "thr_server_wait", "thr_server_stats", "thr_server_free", "thr_rle_encode_rows",
-               "thr_rle_slice", "thr_rle_stitch", "thr_query_sym",
+               "thr_rle_slice", "thr_rle_stitch", "thr_query_sym", "thr_query_opt",
+               "thr_query_opt_batch",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -83,6 +84,9 @@ def load():
             lib.thr_rle_encode_rows.argtypes = [vp, u64, u64, vp, u64, u64p]
             lib.thr_rle_slice.argtypes = [vp, u64, u64, u64, u64, vp, u64, u64p]
             lib.thr_query_sym.argtypes = [vp, vp, u32, u32, u32, vp, u64, u64p, u32, vp]
+            lib.thr_query_opt.argtypes = [vp, vp, u32, u64, u32p, vp, u64, u64p, u32, vp]
+            lib.thr_query_opt_batch.argtypes = [vp, u32, vp, vp, vp, vp, vp, u64, vp, vp, u32,
+                                                vp]
             lib.thr_rle_stitch.argtypes = [vp, vp, vp, u32, vp, u64, u64p]
             lib.thr_last_error.argtypes = []
             lib.thr_last_error.restype = ctypes.c_char_p
@@ -260,6 +264,58 @@ def thr_query_sym(idx: Index, ids, lo: int = 0, hi: int | None = None, odd: bool
                              ctypes.byref(n), flags, ctypes.c_void_p(_stream(stream))),
            "thr_query_sym")
     return n.value
+
+
+def thr_query_opt(idx: Index, ids, K: int = 1, out=None, stream=None, flags: int = 0):
+    """Opt-threshold query: the largest T whose T-overlap result over ids
+    holds at least K rows (0 when none does), and that result.  Returns
+    (T, stream) with out=None, else fills a device tensor / host array and
+    returns (T, number of words)."""
+    lib = load()
+    ids = _u32(ids)
+    n = ctypes.c_uint64(0)
+    T = ctypes.c_uint32(0)
+    if out is None:
+        buf = np.empty(idx.nwords + 1, dtype=np.uint64)
+        _check(lib.thr_query_opt(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                                 ids.size, int(K), ctypes.byref(T),
+                                 ctypes.c_void_p(buf.ctypes.data), buf.size, ctypes.byref(n),
+                                 flags, ctypes.c_void_p(_stream(stream))), "thr_query_opt")
+        return T.value, buf[: n.value].copy()
+    if getattr(out, "is_cuda", False):
+        flags |= THR_OUT_DEVICE
+    size = out.numel() if hasattr(out, "numel") else out.size
+    _check(lib.thr_query_opt(ctypes.c_void_p(idx.handle), ctypes.c_void_p(ids.ctypes.data),
+                             ids.size, int(K), ctypes.byref(T), ctypes.c_void_p(_ptr(out)),
+                             int(size), ctypes.byref(n), flags,
+                             ctypes.c_void_p(_stream(stream))), "thr_query_opt")
+    return T.value, n.value
+
+
+def thr_query_opt_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None):
+    """Batch of (ids, K) opt-threshold queries.  Returns (T, out_off,
+    out_len, pool); with pool=None a host pool of the worst-case size is
+    allocated."""
+    lib = load()
+    nq, id_off, ids, _ = _pack([(q[0], 0) for q in queries])
+    K = _u64([q[1] for q in queries])
+    T = np.zeros(nq, dtype=np.uint32)
+    if pool is None:
+        pool = np.empty(max(nq * (idx.nwords + 1), 1), dtype=np.uint64)
+    if getattr(pool, "is_cuda", False):
+        flags |= THR_OUT_DEVICE
+    size = pool.numel() if hasattr(pool, "numel") else pool.size
+    out_off = np.zeros(nq, dtype=np.uint64)
+    out_len = np.zeros(nq, dtype=np.uint64)
+    _check(lib.thr_query_opt_batch(ctypes.c_void_p(idx.handle), nq,
+                                   ctypes.c_void_p(id_off.ctypes.data),
+                                   ctypes.c_void_p(ids.ctypes.data if ids.size else 0),
+                                   ctypes.c_void_p(K.ctypes.data), ctypes.c_void_p(T.ctypes.data),
+                                   ctypes.c_void_p(_ptr(pool)), int(size),
+                                   ctypes.c_void_p(out_off.ctypes.data),
+                                   ctypes.c_void_p(out_len.ctypes.data), int(flags),
+                                   ctypes.c_void_p(_stream(stream))), "thr_query_opt_batch")
+    return T, out_off, out_len, pool
 
 
 def thr_query_raw(idx: Index, ids, T: int, out_ptr: int, cap: int, flags: int,

@@ -133,27 +133,42 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
 void form_groups(const BatchInput& in, uint32_t q0, uint32_t Q, std::vector<QDesc>& qd,
                  std::vector<uint8_t>& qcls, std::vector<uint2>& grp,
                  std::vector<uint32_t>& memb, std::vector<uint8_t>& absorbed) {
-    std::vector<std::pair<uint64_t, uint32_t>> keys;  // (hash of sorted ids, slot)
-    std::vector<std::vector<uint32_t>> sorted(Q);
+    // an order-independent hash of each multiset (a sum of mixed ids), so
+    // that only queries whose hashes meet are sorted and compared
+    std::vector<std::pair<uint64_t, uint32_t>> keys;  // (hash, slot)
+    keys.reserve(Q);
     for (uint32_t s = 0; s < Q; ++s) {
         const uint32_t q = q0 + s;
         if (class_family(qcls[q]) != 0 || qd[q].sym != kSymThreshold) continue;
-        sorted[s].assign(in.ids + in.id_off[q], in.ids + in.id_off[q + 1]);
-        std::sort(sorted[s].begin(), sorted[s].end());
-        uint64_t h = fnv(14695981039346656037ull, sorted[s].size());
-        for (uint32_t v : sorted[s]) h = fnv(h, v);
+        uint64_t h = fnv(14695981039346656037ull, in.id_off[q + 1] - in.id_off[q]);
+        for (uint32_t i = in.id_off[q]; i < in.id_off[q + 1]; ++i) {
+            uint64_t z = uint64_t(in.ids[i]) + 0x9E3779B97F4A7C15ull;  // splitmix64 finaliser
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            h += z ^ (z >> 31);
+        }
         keys.emplace_back(h, s);
     }
     std::sort(keys.begin(), keys.end());
     int cnt = 0;
     const KernelEntry* tab = kernel_table(&cnt);
+    auto sorted_ids = [&](uint32_t s) {
+        std::vector<uint32_t> v(in.ids + in.id_off[q0 + s], in.ids + in.id_off[q0 + s + 1]);
+        std::sort(v.begin(), v.end());
+        return v;
+    };
     for (size_t i = 0; i < keys.size();) {
         size_t j = i + 1;
         while (j < keys.size() && keys[j].first == keys[i].first) ++j;
+        if (j - i < 2) {
+            i = j;
+            continue;
+        }
         // exact matches only (hash collisions stay apart)
+        const std::vector<uint32_t> lead_ids = sorted_ids(keys[i].second);
         std::vector<uint32_t> mem{keys[i].second};
         for (size_t k = i + 1; k < j; ++k)
-            if (sorted[keys[k].second] == sorted[keys[i].second]) mem.push_back(keys[k].second);
+            if (sorted_ids(keys[k].second) == lead_ids) mem.push_back(keys[k].second);
         i = j;
         if (mem.size() < 2) continue;
         std::sort(mem.begin(), mem.end());

@@ -25,6 +25,7 @@
 #include "thr_index.h"
 #include "thr_batch.h"
 #include "thr_launch.h"
+#include "thr_opt_host.h"
 
 using namespace thr;
 
@@ -565,6 +566,65 @@ thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, 
        "copy result");
     CK(cudaStreamSynchronize(st), "copy result");
     return THR_OK;
+}
+
+thr_status thr_query_opt_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                               const uint32_t* ids, const uint64_t* K, uint32_t* T_out,
+                               uint64_t* pool, uint64_t pool_cap, uint64_t* out_off,
+                               uint64_t* out_len, uint32_t flags, void* cuda_stream) {
+    if (!idx || !id_off || !K || !T_out || !out_off || !out_len || (pool_cap > 0 && !pool))
+        return fail(THR_E_INVAL, "null argument");
+    if (nq == 0) return THR_OK;
+    if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK |
+                  THR_NO_GRAPH | THR_NO_SHARE))
+        return fail(THR_E_INVAL, "unknown flags");
+    if (id_off[0] != 0) return fail(THR_E_INVAL, "id_off[0] must be 0");
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
+        const uint32_t n = id_off[q + 1] - id_off[q];
+        if (n == 0 || n > 65535)
+            return fail(THR_E_INVAL, "query %u: n must be in 1..65535", q);
+        if (K[q] == 0) return fail(THR_E_INVAL, "query %u: K must be >= 1", q);
+    }
+    if (!ids) return fail(THR_E_INVAL, "null ids");
+    for (uint64_t i = 0; i < id_off[nq]; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    float ms = 0.f;
+    thr_status s = opt_profile(idx, nq, id_off, ids, K, T_out, st,
+                               (flags & THR_PROFILE) ? &ms : nullptr);
+    if (s != THR_OK) return s;
+    s = thr_query_batch(idx, nq, id_off, ids, T_out, pool, pool_cap, out_off, out_len,
+                        flags & ~THR_PROFILE, cuda_stream);
+    if (flags & THR_PROFILE) g_kernel_ms = ms;
+    return s;
+}
+
+thr_status thr_query_opt(const thr_index* idx, const uint32_t* ids, uint32_t n, uint64_t K,
+                         uint32_t* T_out, uint64_t* out, uint64_t cap, uint64_t* out_len,
+                         uint32_t flags, void* cuda_stream) {
+    if (!idx || !ids || !T_out || !out_len || (cap > 0 && !out))
+        return fail(THR_E_INVAL, "null argument");
+    if (n == 0 || n > 65535) return fail(THR_E_INVAL, "n must be in 1..65535");
+    if (K == 0) return fail(THR_E_INVAL, "K must be >= 1");
+    if (flags & ~(THR_OUT_DEVICE | THR_PROFILE | THR_VARIANT_MASK))
+        return fail(THR_E_INVAL, "unknown flags");
+    if (variant_of_flag(flags & THR_VARIANT_MASK) < 0)
+        return fail(THR_E_INVAL, "unknown variant");
+    for (uint32_t i = 0; i < n; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    if ((flags & THR_OUT_DEVICE) && cap > 0 && !is_device_ptr(out))
+        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+    const uint32_t id_off[2] = {0, n};
+    float ms = 0.f;
+    thr_status s = opt_profile(idx, 1, id_off, ids, &K, T_out, (cudaStream_t)cuda_stream,
+                               (flags & THR_PROFILE) ? &ms : nullptr);
+    if (s != THR_OK) return s;
+    s = thr_query(idx, ids, n, *T_out, out, cap, out_len, flags & ~THR_PROFILE, cuda_stream);
+    if (flags & THR_PROFILE) g_kernel_ms = ms;
+    return s;
 }
 
 thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,

@@ -95,11 +95,14 @@ struct QDesc {
     uint32_t zmode;
     uint32_t Tlo, Thi;
     uint32_t hi;       // range queries: the upper bound
-    uint32_t sym;      // kSymThreshold, kSymRange or kSymOdd
+    uint32_t sym;      // kSymThreshold, kSymRange, kSymOdd (or kSymProfile)
 };
 // What a query computes from the count c of a row: c >= T (threshold),
 // T <= c <= hi (range: at most, exactly, between), c odd (the XOR).
 constexpr uint32_t kSymThreshold = 0, kSymRange = 1, kSymOdd = 2;
+// Not a result kind: the profiling pass of opt-threshold queries (thr_opt.cuh),
+// whose T is the current lower bound on the answer.
+constexpr uint32_t kSymProfile = 3;
 
 // Pass A of one launch: the queries (slots of the chunk) in list[0..nlist),
 // one work item per (query, subtile), query-major (order 0) or subtile-major

@@ -1,0 +1,20 @@
+// Profiling pass of opt-threshold queries (thr_opt.cuh, thr_opt_host.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/thr.h"
+
+struct thr_index;
+
+namespace thr {
+// For each query q of the batch (ids id_off[q] .. id_off[q+1], already
+// checked), T[q] = the largest T whose T-overlap result holds at least K[q]
+// rows (0 when none does).  Synchronises st; *ms (optional) receives the
+// profiling kernels' time.
+thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                       const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
+                       float* ms);
+}  // namespace thr

@@ -52,6 +52,8 @@ struct QView {
         const uint32_t s = w.qsym;
         const int64_t lo = int64_t(w.qT) - int64_t(k);
         if (s == kSymOdd) return d == 0;
+        // profiling pass: nothing reaches the bound, or no input to count
+        if (s == kSymProfile) return lo > int64_t(d) || d == 0;
         if (s == kSymRange)
             return int64_t(w.qhi) < int64_t(k) || lo > int64_t(d) ||
                    (lo <= 0 && int64_t(k) + int64_t(d) <= int64_t(w.qhi));
@@ -232,6 +234,9 @@ static_assert(kGroup == 2 || kGroup == 4, "inputs are added in fours or twos");
 template <int S>
 struct CsaCount {
     static constexpr bool kSymmetric = true;  // range and parity tests
+    // group members finished inline: below 7 bits the 4-CTA register bound
+    // applies anyway; wider counters finish them out of line (finish_group)
+    static constexpr bool kInlineGroups = S <= 6;
     Counters<S> cnt;
     // the lowest slice is the parity of the count (never saturated)
     __device__ __forceinline__ void parity(uint64_t (&o)[kRows], uint32_t flip) const {
@@ -395,7 +400,8 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
             const int64_t tp = int64_t(q.T()) - int64_t(k_ones);
             if (!kPart && q.sym() != kSymOdd && tp >= 4 && 4 * tp >= int64_t(d_act) &&
                 int64_t(max_position_count<kPos>(p, ws, nrec, nrun, nmix, lane)) < tp) {
-                d_act = 0;  // finish: T' > d, every row zero
+                k_ones = 0;  // finish: T > k + d, every row zero
+                d_act = 0;
                 break;
             }
         } else if (kPart) {
@@ -637,6 +643,25 @@ __device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws
     if (lane == 0) agg_store_plain(p.aggs + sg * kAggWords, L.A);
 }
 
+// The members of a group (queries over the same id multiset, counted
+// once): every member's compare and re-encoding of the subtile.  Out of
+// line, with the counters passed in local memory, so that keeping them
+// across the members' re-encodings does not raise the register count (and
+// lower the occupancy) of the single-query path that shares the kernel;
+// used for counters of 7 bits and more (Count::kInlineGroups).
+template <class Count>
+__device__ __noinline__ void finish_group(const PassAParams& p, WarpSmem& ws, uint2 grp,
+                                          uint32_t g, uint32_t x0, uint32_t x1, uint32_t lane,
+                                          uint32_t k_ones, uint32_t d_act, Count* count) {
+    for (uint32_t i = 0; i < grp.y; ++i) {
+        const uint32_t m = __ldg(p.memb + grp.x + i);
+        uint64_t orow[kRows];
+        finish_subtile(p, p.qd[m].T, 0u, 0u, kSymThreshold, k_ones, d_act, x0, lane, *count,
+                       orow);
+        store_subtile(p, ws, m, g, x0, x1, lane, orow);
+    }
+}
+
 // Pass A driver: each warp of the persistent grid takes every (grid
 // warps)-th work item of the launch, or with a work counter the next free
 // one, an item being one (query, subtile) pair: query-major
@@ -690,13 +715,16 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
             finish_subtile(p, q.T(), q.zmode(), q.hi(), q.sym(), k_ones, d_act, x0, lane, count,
                            orow);
             store_subtile(p, ws, cur, g, x0, x1, lane, orow);
-        } else {  // one count, every member's threshold (ones counted)
+        } else if constexpr (Count::kInlineGroups) {  // one count, every member's threshold
             for (uint32_t i = 0; i < grp.y; ++i) {
                 const uint32_t m = __ldg(p.memb + grp.x + i);
                 finish_subtile(p, p.qd[m].T, 0u, 0u, kSymThreshold, k_ones, d_act, x0, lane,
                                count, orow);
                 store_subtile(p, ws, m, g, x0, x1, lane, orow);
             }
+        } else {
+            Count copy = count;  // the callee reads this copy, count stays in registers
+            finish_group(p, ws, grp, g, x0, x1, lane, k_ones, d_act, &copy);
         }
         it = p.work ? __shfl_sync(~0u, next, 0) : it + nwarps;
     }
@@ -708,7 +736,8 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
 // registers: 7% faster than 8 CTAs for the grouped decode, 28% for the
 // position-major one, whose spills vanish), 4 up to S = 6, 2 beyond.
 template <int S, bool kPos>
-__global__ void __launch_bounds__(kNT, (S <= 3 ? 6 : (S <= 6 ? 4 : 2))) k_threshold(const PassAParams p) {
+__global__ void __launch_bounds__(kNT, (S <= 3 ? 6 : (S <= 6 ? 4 : (S <= 8 ? 3 : 2))))
+    k_threshold(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     CsaCount<S> count;

@@ -19,6 +19,7 @@ constexpr uint32_t kCounterBytes = kRowsPerWord * kGW;  // per warp
 
 struct ScanCount {
     static constexpr bool kSymmetric = false;  // thresholds only
+    static constexpr bool kInlineGroups = true;  // never in a group
     unsigned char* cnt;
     uint32_t lane;
     uint32_t cf[kRows];  // ones-fill words seen at the lane's word of row r
