@@ -65,11 +65,15 @@ def parse():
     ap.add_argument("--profile-query", type=int, default=None, metavar="T",
                     help="build the workload, run one warm-up query at threshold T and "
                          "then one more (the launch to capture with a profiler); no timing")
-    ap.add_argument("--variant", default="csa", choices=["csa", "position", "scancount"],
+    ap.add_argument("--variant", default="csa",
+                    choices=["csa", "position", "scancount", "looped"],
                     help="counting variant of --profile-query")
     ap.add_argument("--batch", action="store_true",
                     help="with --profile-query: the step's four thresholds as one batched "
                          "call (shared counting pass) instead of one query")
+    ap.add_argument("--profile-opt", type=int, default=None, metavar="K",
+                    help="like --profile-query for the opt-threshold query with K rows "
+                         "(profiling pass, then the threshold query)")
     return ap.parse_args()
 
 
@@ -300,6 +304,15 @@ def run_ours(args):
             ts = [plain_query(T, vflag)[1] for _ in range(max(args.steps, 3))]
             per_t[str(T)] = round(statistics.median(ts), 5)
         variant_ms[vname] = per_t
+    # Looped levels (T <= 4 only; T = 1 and 2 on these bitmaps) next to carry-save
+    saved_out = dict(out_words)
+    variant_ms["looped_vs_csa"] = {
+        str(T): {v: round(statistics.median(
+            [plain_query(T, f)[1] for _ in range(max(args.steps, 3))]), 5)
+            for v, f in (("looped", thr.THR_VARIANT_LOOPED), ("csa", thr.THR_VARIANT_CSA))}
+        for T in (1, 2)}
+    out_words.clear()
+    out_words.update(saved_out)
     # symmetric functions of the same counts (at most 1, exactly 2, 2..4, odd)
     sym_ms = {}
     for name, lo, hi, odd in (("at_most_1", 0, 1, False), ("exactly_2", 2, 2, False),
@@ -493,12 +506,14 @@ def profile_query(args):
     r, gw, goff = make_index_inputs(args.seed)
     idx = thr.idx_build_rle(gw, goff, r)
     flag = {"csa": thr.THR_VARIANT_CSA, "position": thr.THR_VARIANT_POSITION,
-            "scancount": thr.THR_VARIANT_SCANCOUNT}[args.variant]
+            "scancount": thr.THR_VARIANT_SCANCOUNT, "looped": thr.THR_VARIANT_LOOPED}[args.variant]
     ids = np.arange(synth.MANY_N, dtype=np.uint32)
     dout = torch.empty(idx.nwords + 1, dtype=torch.int64, device="cuda")
     pool = torch.empty(4 * (idx.nwords + 1), dtype=torch.int64, device="cuda")
     for _ in range(2):
-        if args.batch:
+        if args.profile_opt is not None:
+            T, n = thr.thr_query_opt(idx, ids, args.profile_opt, out=dout)
+        elif args.batch:
             _, ln, _ = thr.thr_query_batch(idx, [(ids, T) for T in synth.MANY_TS], pool=pool,
                                            flags=flag | thr.THR_NO_GRAPH)
             n = int(ln.sum())
@@ -512,7 +527,7 @@ def profile_query(args):
 
 def main():
     args = parse()
-    if args.profile_query is not None:
+    if args.profile_query is not None or args.profile_opt is not None:
         profile_query(args)
     elif args.impl == "reference":
         run_reference(args)

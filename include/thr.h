@@ -89,11 +89,17 @@ typedef enum {
  *                          among the four warps of a CTA, whose counters are
  *                          then added: more parallelism for queries with
  *                          few subtiles (small r) and many inputs; used when
- *                          the counters need at most 8 bits, else CSA runs */
+ *                          the counters need at most 8 bits, else CSA runs
+ *   THR_VARIANT_LOOPED     Looped (Sec. 6.2, Algorithm 3): T bitmaps C_1..C_T
+ *                          per word, C_j = rows counted at least j times so
+ *                          far, each input one AND-OR per level; used when
+ *                          1 <= T <= 4 and T <= n, else CSA runs.  Not an arm
+ *                          of the rule or learned policies. */
 #define THR_VARIANT_CSA 0x000u
 #define THR_VARIANT_SCANCOUNT 0x200u
 #define THR_VARIANT_POSITION 0x400u
 #define THR_VARIANT_SPLIT 0x600u
+#define THR_VARIANT_LOOPED 0x800u
 #define THR_VARIANT_MASK 0xE00u
 
 /*

@@ -30,6 +30,7 @@ THR_NO_SHARE = 0x2000
 THR_SYM_ODD = 0x4000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 THR_VARIANT_SPLIT = 0x600
+THR_VARIANT_LOOPED = 0x800
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",

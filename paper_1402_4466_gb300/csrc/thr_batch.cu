@@ -278,17 +278,17 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         ChunkPlan ch{q0, Q, uint32_t(launches.size()), 0};
         if (opt.share) form_groups(in, q0, Q, qd, qcls, grp, memb, absorbed);
         // the chunk's shape and its launch configuration
-        uint32_t present = 0;
+        uint64_t present = 0;
         double sum_n = 0;
-        int widest[4] = {-1, -1, -1, -1};  // per family
+        int widest[kNumFamilies] = {-1, -1, -1, -1, -1};  // per family
         for (uint32_t s = 0; s < Q; ++s) {
             if (absorbed[q0 + s]) continue;
             const int c = qcls[q0 + s];
-            present |= 1u << c;
+            present |= uint64_t(1) << c;
             sum_n += qd[q0 + s].n;
             widest[class_family(c)] = std::max(widest[class_family(c)], c);
         }
-        const bool multi = __builtin_popcount(present) > 1;
+        const bool multi = __builtin_popcountll(present) > 1;
         const uint32_t shape = tune_key(multi, sum_n / Q);
         if (q0 == 0) first_key = shape;
         uint32_t cfg = opt.force_tune >= 0 ? uint32_t(opt.force_tune) : tune_lookup(idx, shape);

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -318,6 +319,8 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
     idx->total_words = total;
     idx->desc.resize(nbitmaps);
     idx->set_rows.resize(nbitmaps);
+    idx->feat_lw.resize(nbitmaps);
+    idx->feat_ld.resize(nbitmaps);
     uint64_t moff = 0;
     for (uint32_t b = 0; b < nbitmaps; ++b) {
         BitmapDesc& d = idx->desc[b];
@@ -327,6 +330,8 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         d.len = uint32_t(offsets[b + 1] - offsets[b]);
         moff += d.nmark + 1;
         idx->set_rows[b] = scans[b].set_rows;
+        idx->feat_lw[b] = std::log2(double(d.len) + 1.0);
+        idx->feat_ld[b] = std::log10(double(scans[b].set_rows) / double(r) + 1e-7);
     }
     idx->total_markers = moff - nbitmaps;
     std::vector<uint32_t> mpos;
@@ -498,7 +503,8 @@ thr_status thr_select_variants(const thr_index* idx, uint32_t nq, const uint32_t
         // the variant that actually runs (fallbacks of ScanCount and split)
         const int fam = class_family(cls);
         variant[q] = uint8_t(fam == 0 ? kVarCsa : fam == 1 ? kVarScanCount
-                                                : fam == 2 ? kVarPos : kVarSplit);
+                                                : fam == 2 ? kVarPos : fam == 3 ? kVarSplit
+                                                                              : kVarLooped);
     }
     return THR_OK;
 }

@@ -22,6 +22,9 @@ int bits_of(uint64_t v) {
 
 cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t st) {
     if (cls == kClassScanCount) return launch_scancount(p, grid, st);
+    if (class_family(cls) == 4)
+        return cls < kNumClasses ? launch_looped(cls - kClassLooped + 1, p, grid, st)
+                                 : cudaErrorInvalidValue;
     int cnt = 0;
     const KernelEntry* tab = kernel_table(&cnt);
     const int w = class_width(cls);
@@ -84,6 +87,11 @@ void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode) {
 }
 
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
+    if (v == kVarLooped && T >= 1 && T <= uint32_t(kLoopedMax) && T <= n) {
+        *cls = kClassLooped + int(T) - 1;
+        *zmode = 0;
+        return;
+    }
     if (v == kVarScanCount && n <= 255) {
         *cls = kClassScanCount;
         *zmode = 0;
@@ -111,6 +119,9 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
 
 cudaError_t class_occupancy(int cls, int* per_sm) {
     if (cls == kClassScanCount) return occupancy_scancount(per_sm);
+    if (class_family(cls) == 4)
+        return cls < kNumClasses ? occupancy_looped(cls - kClassLooped + 1, per_sm)
+                                 : cudaErrorInvalidValue;
     int cnt = 0;
     const KernelEntry* tab = kernel_table(&cnt);
     const int w = class_width(cls);

@@ -17,22 +17,30 @@ namespace thr {
 // kernel_table()[c].S (grouped decode), kClassScanCount the ScanCount
 // kernel, kClassPos + c carry-save of width kernel_table()[c].S with the
 // position-major decode of mixed inputs, kClassSplit + c carry-save with
-// the inputs split among the CTA's warps (widths up to kSplitWidths).
+// the inputs split among the CTA's warps (widths up to kSplitWidths),
+// kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax).
 constexpr int kNumWidths = 11;
 constexpr int kSplitWidths = 8;  // S = 1..8
+constexpr int kLoopedMax = 4;    // Looped levels (thresholds) instantiated
 constexpr int kClassScanCount = kNumWidths;
 constexpr int kClassPos = kNumWidths + 1;
 constexpr int kClassSplit = 2 * kNumWidths + 1;
-constexpr int kNumClasses = kClassSplit + kSplitWidths;
-static_assert(kNumClasses <= 32, "class sets are 32-bit masks");
+constexpr int kClassLooped = kClassSplit + kSplitWidths;
+constexpr int kNumClasses = kClassLooped + kLoopedMax;
+static_assert(kNumClasses <= 64, "class sets are 64-bit masks");
 // Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major,
-// 3 split inputs.
+// 3 split inputs, 4 Looped.
+constexpr int kNumFamilies = 5;
 inline int class_family(int c) {
-    return c < kNumWidths ? 0 : (c == kClassScanCount ? 1 : (c < kClassSplit ? 2 : 3));
+    return c < kNumWidths ? 0
+                          : (c == kClassScanCount ? 1
+                                                  : (c < kClassSplit ? 2 : (c < kClassLooped ? 3 : 4)));
 }
-// Counter-width index of a carry-save class.
+// Counter-width index of a carry-save class (levels - 1 for Looped).
 inline int class_width(int c) {
-    return c < kNumWidths ? c : (c < kClassSplit ? c - kClassPos : c - kClassSplit);
+    return c < kNumWidths ? c
+                          : (c < kClassSplit ? c - kClassPos
+                                             : (c < kClassLooped ? c - kClassSplit : c - kClassLooped));
 }
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
@@ -101,7 +109,10 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
 //   kVarSplit      grouped carry-save with each subtile's inputs split among
 //                  the four warps of a CTA (S <= 8; else kVarCsa runs)
 constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2, kVarSplit = 3;
-constexpr int kNumVariants = 4;
+constexpr int kNumVariants = 4;  // the policies' choices
+//   kVarLooped     Looped levels (Sec. 6.2) for 1 <= T <= kLoopedMax, T <= n
+//                  (else kVarCsa runs); chosen by flag only
+constexpr int kVarLooped = 4;
 // Kernel class and zero counting of a query run with variant v.
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 

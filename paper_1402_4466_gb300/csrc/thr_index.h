@@ -31,6 +31,9 @@ struct thr_index {
     thr::BitmapDesc* d_desc = nullptr;
     std::vector<thr::BitmapDesc> desc;
     std::vector<uint64_t> set_rows;
+    // per bitmap, the selector's feature terms log2(words + 1) and
+    // log10(density + 1e-7), computed once at build
+    std::vector<double> feat_lw, feat_ld;
     int num_sms = 0;
     // pass-A launch configurations chosen by thr_autotune, per batch shape
     mutable std::mutex tune_mu;

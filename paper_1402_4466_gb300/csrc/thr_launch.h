@@ -25,6 +25,10 @@ struct KernelEntry {
 cudaError_t launch_scancount(const PassAParams&, int grid, cudaStream_t);
 cudaError_t occupancy_scancount(int* blocks_per_sm);
 
+// Pass A with Looped levels (thr_inst_looped.cu), M = 1 .. kLoopedMax.
+cudaError_t launch_looped(int M, const PassAParams&, int grid, cudaStream_t);
+cudaError_t occupancy_looped(int M, int* blocks_per_sm);
+
 // Instantiated counter widths, ascending; a query uses the first S with
 // 2^S > the largest threshold its counters test.
 const KernelEntry* kernel_table(int* count);

@@ -270,6 +270,50 @@ struct CsaCount {
     }
 };
 
+// Counting policy of the Looped variant (Algorithm 3, Sec. 6.2): M bitmaps
+// C_1 .. C_M per 32-bit half word, C_j holding the rows counted at least j
+// times so far.  An input x updates C_j |= C_(j-1) & x for j = M .. 2 (one
+// LOP3 each), then C_1 |= x; the rows reaching T' <= M are C_(T').  Ones
+// only (the host never sets zmode for it); absent inputs of a group are zero
+// words, which change nothing.
+template <int M>
+struct LoopedCount {
+    static constexpr bool kSymmetric = false;    // thresholds only
+    static constexpr bool kInlineGroups = true;  // never in a group
+    uint32_t C[M][8];
+    __device__ __forceinline__ void begin() {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+#pragma unroll
+            for (int h = 0; h < 8; ++h) C[j][h] = 0;
+    }
+    __device__ __forceinline__ void add(const uint64_t (&v)[kGroup][kRows], uint32_t) {
+#pragma unroll
+        for (int i = 0; i < kGroup; ++i)
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const uint32_t x = uint32_t(v[i][h >> 1] >> (32 * (h & 1)));
+#pragma unroll
+                for (int j = M - 1; j >= 1; --j) C[j][h] = lop3<kOrAnd>(C[j][h], C[j - 1][h], x);
+                C[0][h] |= x;
+            }
+    }
+    // 1 <= thr <= M; flip inverts the result
+    __device__ __forceinline__ void finish(uint32_t thr, uint32_t flip, uint64_t (&o)[kRows]) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                if (uint32_t(j + 1) == thr) {
+                    lo = C[j][2 * r];
+                    hi = C[j][2 * r + 1];
+                }
+            o[r] = (uint64_t(hi ^ flip) << 32) | (lo ^ flip);
+        }
+    }
+};
+
 // One warp computes the 128 result words of subtile [x0, x1); lane owns rows
 // r = 0..3, words x0 + 32 r + lane (zero past x1).  Count is the counting
 // policy (carry-save bit slices, or ScanCount counters).  kPos: mixed inputs
@@ -742,6 +786,15 @@ __global__ void __launch_bounds__(kNT, (S <= 3 ? 6 : (S <= 6 ? 4 : (S <= 8 ? 3 :
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
     CsaCount<S> count;
     pass_a<CsaCount<S>, kPos>(p, sm, count);
+}
+
+// Pass A with the Looped levels (M thresholds at most).
+template <int M>
+__global__ void __launch_bounds__(kNT, 6) k_looped(const PassAParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
+    LoopedCount<M> count;
+    pass_a<LoopedCount<M>, false>(p, sm, count);
 }
 
 // Pass A with the inputs of every subtile split among the CTA's warps: the

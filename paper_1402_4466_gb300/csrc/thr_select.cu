@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "thr_batch.h"
@@ -108,6 +109,7 @@ int variant_of_flag(uint32_t f) {
         case THR_VARIANT_POSITION: return kVarPos;
         case THR_VARIANT_SCANCOUNT: return kVarScanCount;
         case THR_VARIANT_SPLIT: return kVarSplit;
+        case THR_VARIANT_LOOPED: return kVarLooped;
         default: return -1;
     }
 }
@@ -141,11 +143,11 @@ void query_features(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
     std::vector<double> w(n), d(n);
     double sw = 0, sd = 0;
     const double r = double(idx->r);
-    for (uint32_t i = 0; i < n; ++i) {
+    for (uint32_t i = 0; i < n; ++i) {  // log terms precomputed per bitmap at build
         const double words = double(idx->desc[ids[i]].len);
         const double dens = double(idx->set_rows[ids[i]]) / r;
-        w[i] = std::log2(words + 1.0);
-        d[i] = std::log10(dens + 1e-7);
+        w[i] = idx->feat_lw[ids[i]];
+        d[i] = idx->feat_ld[ids[i]];
         sw += words;
         sd += dens;
     }
@@ -192,9 +194,25 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
     *used = false;
     if (!sel) return THR_OK;
     std::vector<float> X(size_t(nq) * kSelFeatures), Y(size_t(nq) * kSelVariants);
-    for (uint32_t q = 0; q < nq; ++q)
-        query_features(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
-                       &X[size_t(q) * kSelFeatures]);
+    auto features = [&](uint32_t q0, uint32_t q1) {
+        for (uint32_t q = q0; q < q1; ++q)
+            query_features(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q],
+                           &X[size_t(q) * kSelFeatures]);
+    };
+    // large batches: the features on a few host threads
+    const uint32_t nthreads =
+        nq >= 1024 ? std::min<uint32_t>(8, std::max(1u, std::thread::hardware_concurrency()))
+                   : 1;
+    if (nthreads > 1) {
+        std::vector<std::thread> pool;
+        for (uint32_t t = 1; t < nthreads; ++t)
+            pool.emplace_back(features, uint32_t(uint64_t(nq) * t / nthreads),
+                              uint32_t(uint64_t(nq) * (t + 1) / nthreads));
+        features(0, uint32_t(nq / nthreads));
+        for (auto& th : pool) th.join();
+    } else {
+        features(0, nq);
+    }
     thr_status s = sel->predict(X.data(), nq, Y.data());
     if (s != THR_OK) return s;
     // another variant replaces the default only when it is predicted at

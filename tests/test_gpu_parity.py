@@ -306,6 +306,41 @@ def test_split_many_criteria_full_size(many_criteria_full):
         p.check(list(range(synth.MANY_N)), T, SPLIT)
 
 
+# ---- the Looped levels (Algorithm 3, Sec. 6.2) for T <= 4
+
+LOOPED = thr.THR_VARIANT_LOOPED
+
+
+def test_looped_random_tiny_all_thresholds():
+    rng = np.random.default_rng(606)
+    for _ in range(20):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        ids = rng.integers(0, n, int(rng.integers(1, 2 * n + 1))).tolist()
+        for T in range(0, len(ids) + 2):  # T > 4 and T > n fall back to carry-save
+            p.check(ids, T, LOOPED)
+
+
+def test_looped_several_tiles_chunks_and_full_size(many_criteria_full):
+    r = (1 << 18) + 3
+    words, _ = synth.many_criteria(19, 30, r)
+    p = Pair(words, r)
+    rng = np.random.default_rng(20)
+    for ids in (list(range(30)), rng.integers(0, 30, size=300).tolist()):
+        for T in (1, 2, 3, 4, 5):
+            p.check(ids, T, LOOPED)
+    words, r = many_criteria_full
+    p = Pair(words, r)
+    for T in (1, 2, 3, 4):
+        p.check(list(range(synth.MANY_N)), T, LOOPED)
+    # in a batch, next to carry-save queries
+    qs = [(list(range(synth.MANY_N)), T) for T in (2, 4, 16)]
+    off, ln, pool = thr.thr_query_batch(p.g, qs, flags=LOOPED)
+    for k, (ids, T) in enumerate(qs):
+        assert np.array_equal(pool[int(off[k]): int(off[k] + ln[k])], p.o.threshold(ids, T))
+
+
 # ---- symmetric functions of the counts: ranges and odd counts
 
 def _check_sym(p, ids, lo, hi, odd=False):
