@@ -348,6 +348,7 @@ thr_status Selector::set_params(const float* host) {
     k_round<<<(kParams + 255) / 256, 256>>>(p, q, kParams);
     CKM(cudaGetLastError(), "round parameters");
     CKM(cudaDeviceSynchronize(), "round parameters");
+    bump_version();
     return THR_OK;
 }
 
@@ -361,12 +362,56 @@ thr_status Selector::set_norm(const float* mean, const float* istd) {
     CKM(cudaMemcpy(norm + F, istd, sizeof(float) * F, cudaMemcpyHostToDevice), "norm");
     std::memcpy(h_norm, mean, sizeof(float) * F);
     std::memcpy(h_norm + F, istd, sizeof(float) * F);
+    bump_version();
     return THR_OK;
+}
+
+void Selector::bump_version() {
+    std::lock_guard<std::mutex> lk(pmu);
+    ++version;
 }
 
 thr_status Selector::predict(const float* X, uint32_t rows, float* Y) const {
     if (!rows) return THR_OK;
     std::lock_guard<std::mutex> lk(pmu);
+    return forward_locked(X, rows, Y);
+}
+
+thr_status Selector::predict_memo(const float* X, uint32_t rows, float* Y) const {
+    if (!rows) return THR_OK;
+    std::lock_guard<std::mutex> lk(pmu);
+    if (memo_version != version || memo.size() > 65536) {
+        memo.clear();
+        memo_version = version;
+    }
+    std::vector<uint32_t> miss;
+    for (uint32_t i = 0; i < rows; ++i) {
+        auto it = memo.find(std::string(reinterpret_cast<const char*>(X + size_t(F) * i),
+                                        sizeof(float) * F));
+        if (it == memo.end()) {
+            miss.push_back(i);
+        } else {
+            std::memcpy(Y + size_t(V) * i, it->second.data(), sizeof(float) * V);
+        }
+    }
+    if (miss.empty()) return THR_OK;
+    std::vector<float> mx(size_t(F) * miss.size()), my(size_t(V) * miss.size());
+    for (size_t k = 0; k < miss.size(); ++k)
+        std::memcpy(&mx[F * k], X + size_t(F) * miss[k], sizeof(float) * F);
+    thr_status s = forward_locked(mx.data(), uint32_t(miss.size()), my.data());
+    if (s != THR_OK) return s;
+    for (size_t k = 0; k < miss.size(); ++k) {
+        std::array<float, kSelVariants> y;
+        std::memcpy(y.data(), &my[V * k], sizeof(float) * V);
+        std::memcpy(Y + size_t(V) * miss[k], y.data(), sizeof(float) * V);
+        memo.emplace(std::string(reinterpret_cast<const char*>(X + size_t(F) * miss[k]),
+                                 sizeof(float) * F),
+                     y);
+    }
+    return THR_OK;
+}
+
+thr_status Selector::forward_locked(const float* X, uint32_t rows, float* Y) const {
     if (!pst) CKM(cudaStreamCreateWithFlags(&pst, cudaStreamNonBlocking), "predict stream");
     if (pcap < rows) {
         cudaFree(pdev);
@@ -466,6 +511,7 @@ thr_status Selector::train(const float* X, const float* Tg, const uint8_t* M, ui
         last = l / float(nbatches);  // mean of the minibatch losses
     }
     if (final_loss) *final_loss = last;
+    bump_version();
     return THR_OK;
 }
 

@@ -4,8 +4,11 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <mutex>
+#include <string>
+#include <unordered_map>
 
 #include "../../include/thr.h"
 
@@ -41,6 +44,11 @@ struct Selector {
     mutable float* phost = nullptr; // pinned staging of the same
     mutable uint32_t pcap = 0;      // rows
     mutable cudaStream_t pst = nullptr;
+    // predictions already made, by feature vector, for the parameters and
+    // normalisation of `version` (bumped by every change of either)
+    uint64_t version = 0;
+    mutable uint64_t memo_version = ~0ull;
+    mutable std::unordered_map<std::string, std::array<float, kSelVariants>> memo;
 
     ~Selector();
     thr_status init(uint64_t seed, bool use_bf16);
@@ -48,6 +56,11 @@ struct Selector {
     thr_status get_params(float* host) const;
     thr_status set_norm(const float* mean, const float* istd);
     thr_status predict(const float* X, uint32_t rows, float* Y) const;
+    // the same predictions, reusing those already made for identical
+    // features (the policy's repeated queries skip the forward pass)
+    thr_status predict_memo(const float* X, uint32_t rows, float* Y) const;
+    thr_status forward_locked(const float* X, uint32_t rows, float* Y) const;  // pmu held
+    void bump_version();  // after a change of parameters or normalisation
     thr_status gradients(const float* X, const float* T, const uint8_t* M, uint32_t rows,
                          float* grad, float* loss_out);
     thr_status train(const float* X, const float* T, const uint8_t* M, uint32_t rows,

@@ -213,7 +213,7 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
     } else {
         features(0, nq);
     }
-    thr_status s = sel->predict(X.data(), nq, Y.data());
+    thr_status s = sel->predict_memo(X.data(), nq, Y.data());
     if (s != THR_OK) return s;
     // another variant replaces the default only when it is predicted at
     // least kSwitchGain faster: a marginal switch costs a batch an extra

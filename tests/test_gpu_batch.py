@@ -131,6 +131,25 @@ def test_graph_replayed_with_new_inputs(mixed):
     _check(g, o, q2, off, ln, pool)
 
 
+def test_identical_plans_relaunch_the_cached_graph(mixed):
+    """Batches of one shape into the same device pool, alternating two id sets
+    (A, B, A, B): when every parameter of the captured work is unchanged the
+    cached executable is launched as it is, reading the new plan from the
+    pinned staging; each result is that of its own queries."""
+    import torch
+    g, o, r = mixed
+    rr = np.random.default_rng(17)
+    qa = [(rr.integers(0, 48, 12).astype(np.uint32), 4) for _ in range(6)]
+    qb = [(rr.integers(0, 48, 12).astype(np.uint32), 4) for _ in range(6)]
+    pool = torch.zeros(6 * (g.nwords + 1), dtype=torch.int64, device="cuda")
+    for qs in (qa, qb, qa, qb):
+        off, ln, _ = thr.thr_query_batch(g, qs, pool=pool)
+        host = pool.cpu().numpy().view(np.uint64)
+        for k, (ids, T) in enumerate(qs):
+            assert np.array_equal(host[int(off[k]): int(off[k] + ln[k])], o.threshold(ids, T))
+    assert thr.thr_last_batch_info()["graph"] == 1
+
+
 def test_batch_many_inputs_per_query(mixed):
     """n above one chunk of input records (128) and above the ScanCount
     limit (255): the uncached id path and the carry-save fallback."""
