@@ -10,8 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <utility>
+#include <chrono>
 #include <cstdio>
+#include <utility>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -121,6 +122,21 @@ uint64_t fnv(uint64_t h, uint64_t v) {
     return h;
 }
 
+// THR_TRACE_TIME=1 in the environment: one stderr line per batch call with
+// the host time (us) at the end of planning, staging, launch and the wait.
+bool trace_time_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("THR_TRACE_TIME");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+double now_us() {
+    return std::chrono::duration<double, std::micro>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 uint64_t env_u64(const char* name, uint64_t dflt) {
     const char* v = std::getenv(name);
     if (!v || !*v) return dflt;
@@ -213,6 +229,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                      const BatchOptions& opt, BatchStats* stats) {
     const uint32_t nq = in.nq;
     const uint32_t W = idx->W, NG = idx->NG;
+    const double t0 = trace_time_on() ? now_us() : 0.0;
+    double t_plan = 0, t_stage = 0, t_launch = 0;
     CKB(g_ctx.init(idx->device), "per-thread streams");
 
     // ---- chunking: as many slots per chunk as the scratch budget allows
@@ -345,6 +363,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         stats->tune_key = first_key;
     }
 
+    if (t0 > 0) t_plan = now_us();
     // ---- device memory: plan (descriptors, ids, lists) | scratch
     const uint64_t nids = in.id_off[nq];
     const size_t o_qd = 0;
@@ -364,6 +383,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     if (!memb.empty()) std::memcpy(pin + o_memb, memb.data(), sizeof(uint32_t) * memb.size());
     unsigned long long* h_res = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
 
+    if (t0 > 0) t_stage = now_us();
     const bool graph = opt.graph && !opt.profile;
     cudaStream_t xs = graph ? g_ctx.cs : st;  // the stream the work is enqueued on
     if (graph) {  // the capture stream starts after the caller's earlier work
@@ -499,7 +519,11 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     } else {
         CKB(enqueue(xs), "enqueue");
     }
+    if (t0 > 0) t_launch = now_us();
     CKB(cudaStreamSynchronize(xs), "batch");
+    if (t0 > 0)
+        std::fprintf(stderr, "[thr] batch nq=%u plan %.1f stage %.1f launch %.1f wait %.1f us\n",
+                     nq, t_plan - t0, t_stage - t_plan, t_launch - t_stage, now_us() - t_launch);
     if (opt.profile) {
         double ms = 0;
         for (size_t c = 0; c < chunks.size(); ++c) {

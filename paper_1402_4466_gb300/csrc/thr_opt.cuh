@@ -25,7 +25,10 @@
 // stopping point and lb never pass the answer), so the histogram's suffix
 // sums from the top are exact down to the answer, and the host takes the
 // first c (from n down) whose suffix holds K rows; 0 when none does.
-// Counters are exact: the kernel runs with 2^S > n.
+// Counters are exact up to 2^S - 1.  The host first runs narrow counters
+// (2^S > min(n, 15)); a subtile in which a row reaches 2^S (the sticky
+// slice) records nothing and flags its query, which then runs again with
+// 2^S > n.
 #pragma once
 
 #include "thr_query_kernel.cuh"
@@ -40,9 +43,12 @@ struct OptParams {
     const unsigned long long* K;     // per query: rows wanted (>= 1)
     uint32_t stride;                 // subtiles 0, stride, 2 stride, ... of each query
     uint32_t record;                 // 0: only raise the bounds (seeding), 1: also the bins
+    uint32_t exact;                  // 1: 2^S > n for every query of the launch
+    uint32_t* ovf;                   // per query: set when a count reached 2^S (exact = 0)
 };
 
-// Occupancy bound: 4 CTAs per SM up to S = 6, 3 up to S = 8, 2 beyond.
+// Occupancy bound: 4 CTAs per SM up to S = 6 (the narrow first pass runs
+// with S <= 4), 3 up to S = 8, 2 beyond.
 template <int S>
 __global__ void __launch_bounds__(kNT, (S <= 6 ? 4 : (S <= 8 ? 3 : 2)))
     k_opt_profile(const OptParams o) {
@@ -89,6 +95,15 @@ __global__ void __launch_bounds__(kNT, (S <= 6 ? 4 : (S <= 8 ? 3 : 2)))
             if (x == p.W - 1 && p.ragged) m = (1ull << p.ragged) - 1;
             vm[2 * r] = uint32_t(m);
             vm[2 * r + 1] = uint32_t(m >> 32);
+        }
+        if (!o.exact && d > 0) {  // a count beyond the counters: this query runs again wider
+            uint32_t sat = 0;
+#pragma unroll
+            for (int h = 0; h < 8; ++h) sat |= count.cnt.sticky[h] & vm[h];
+            if (__any_sync(~0u, sat != 0)) {
+                if (lane == 0) atomicOr(o.ovf + s, 1u);
+                continue;
+            }
         }
         const unsigned long long K = o.K[s];
         unsigned long long* hist = o.hist + o.hoff[s];

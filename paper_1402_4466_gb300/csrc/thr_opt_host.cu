@@ -47,9 +47,15 @@ int occupancy(const OptEntry& e, int slot, int device) {
 
 }  // namespace
 
-thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
-                       const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
-                       float* ms) {
+// Narrow counters first: exact counts up to this bound, then a second pass
+// with 2^S > n for the queries in which some count went beyond it.
+constexpr uint32_t kNarrowCounts = 15;
+
+// One profiling pass over the batch; exact: 2^S > n, else narrow counters,
+// and ovf[q] (host) tells which queries must run again.
+thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                        const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
+                        float* ms, bool exact, std::vector<uint32_t>* ovf_out) {
     int nt = 0;
     const OptEntry* tab = opt_kernel_table(&nt);
     const uint64_t nids = id_off[nq];
@@ -58,8 +64,9 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
     uint64_t nbins = 0;
     for (uint32_t q = 0; q < nq; ++q) {
         const uint32_t n = id_off[q + 1] - id_off[q];
+        const uint32_t need = exact ? n : std::min(n, kNarrowCounts);
         int w = 0;
-        while (w < nt && (uint64_t(1) << tab[w].S) <= n) ++w;
+        while (w < nt && (uint64_t(1) << tab[w].S) <= need) ++w;
         if (w == nt) return report_error(THR_E_INVAL, "opt-threshold query with too many ids");
         width[q] = w;
         ++per_width[w];
@@ -71,7 +78,8 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
     const size_t o_lb = o_hoff + align16(8ull * nq);
     const size_t o_list = o_lb + align16(4ull * nq);
     const size_t o_ids = o_list + align16(4ull * nq);
-    const size_t o_hist = o_ids + align16(4ull * nids);
+    const size_t o_ovf = o_ids + align16(4ull * nids);
+    const size_t o_hist = o_ovf + align16(4ull * nq);
     const size_t total = o_hist + 8ull * nbins;
     std::vector<unsigned char> h(o_hist, 0);
     QDesc* qd = reinterpret_cast<QDesc*>(h.data());
@@ -125,6 +133,8 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
     o.hoff = reinterpret_cast<const unsigned long long*>(d + o_hoff);
     o.lb = reinterpret_cast<uint32_t*>(d + o_lb);
     o.K = reinterpret_cast<const unsigned long long*>(d + o_K);
+    o.exact = exact ? 1u : 0u;
+    o.ovf = reinterpret_cast<uint32_t*>(d + o_ovf);
     constexpr uint32_t kSeedStride = 16;
     for (int w = 0; w < nt; ++w) {
         if (!per_width[w] || idx->NG == 0) continue;
@@ -148,6 +158,11 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
     if (ms) OPT_CK(cudaEventRecord(ev[1], st), "event");
     OPT_CK(cudaMemcpyAsync(hist.data(), d + o_hist, 8ull * nbins, cudaMemcpyDeviceToHost, st),
            "opt bins");
+    if (ovf_out) {
+        ovf_out->assign(nq, 0);
+        OPT_CK(cudaMemcpyAsync(ovf_out->data(), d + o_ovf, 4ull * nq, cudaMemcpyDeviceToHost, st),
+               "opt overflow flags");
+    }
     OPT_CK(cudaStreamSynchronize(st), "opt profiling");
     if (ms) {
         cudaEventElapsedTime(ms, ev[0], ev[1]);
@@ -168,6 +183,37 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
             }
         }
     }
+    return THR_OK;
+}
+
+thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
+                       const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
+                       float* ms) {
+    std::vector<uint32_t> ovf;
+    float ms1 = 0.f;
+    thr_status s =
+        profile_pass(idx, nq, id_off, ids, K, T, st, ms ? &ms1 : nullptr, false, &ovf);
+    if (s != THR_OK) return s;
+    std::vector<uint32_t> redo;
+    for (uint32_t q = 0; q < nq; ++q)
+        if (ovf[q]) redo.push_back(q);
+    if (!redo.empty()) {  // counts beyond the narrow counters: again with 2^S > n
+        std::vector<uint32_t> off2(redo.size() + 1, 0), ids2, T2(redo.size(), 0);
+        std::vector<uint64_t> K2(redo.size());
+        for (size_t i = 0; i < redo.size(); ++i) {
+            const uint32_t q = redo[i];
+            ids2.insert(ids2.end(), ids + id_off[q], ids + id_off[q + 1]);
+            off2[i + 1] = uint32_t(ids2.size());
+            K2[i] = K[q];
+        }
+        float ms2 = 0.f;
+        s = profile_pass(idx, uint32_t(redo.size()), off2.data(), ids2.data(), K2.data(),
+                         T2.data(), st, ms ? &ms2 : nullptr, true, nullptr);
+        if (s != THR_OK) return s;
+        for (size_t i = 0; i < redo.size(); ++i) T[redo[i]] = T2[i];
+        ms1 += ms2;
+    }
+    if (ms) *ms = ms1;
     return THR_OK;
 }
 
