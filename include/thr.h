@@ -314,9 +314,11 @@ thr_status thr_rle_encode_rows(const uint64_t *rows, uint64_t nrows, uint64_t r,
                                uint64_t *out, uint64_t cap, uint64_t *out_len);
 
 /*
- * Device time in milliseconds of the query kernel of the last thr_query
- * call on this thread that passed THR_PROFILE (CUDA events recorded on the
- * query's stream right before and after the kernel launch); -1 if none.
+ * Device time in milliseconds of the counting kernels (pass A) of the last
+ * call on this thread that passed THR_PROFILE (thr_query, thr_query_sym,
+ * thr_query_batch: CUDA events recorded right before and after the pass-A
+ * launches of each chunk, summed; thr_query_opt and thr_query_opt_batch: the
+ * profiling pass); -1 if none.
  */
 double thr_last_kernel_ms(void);
 
@@ -424,6 +426,14 @@ thr_status thr_rule_model(const double *set, double *get);
  */
 thr_status thr_last_batch_info(uint32_t *chunks, uint32_t *launches, int32_t *graph,
                                uint32_t *config);
+
+/*
+ * Diagnostics read from the environment at first use: THR_TRACE=1 prints a
+ * stderr line per step of a query; THR_TRACE_TIME=1 prints, per batch call,
+ * the host time of planning, staging, launch and the wait for the device.
+ * Testing only: THR_TUNE_CONFIG=k forces pass-A launch configuration k and
+ * THR_MAX_SLOTS=m caps the queries per chunk.
+ */
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *thr_last_error(void);
