@@ -110,7 +110,14 @@ thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_of
     } guard{d, st};
     OPT_CK(cudaMemcpyAsync(d, h.data(), o_hist, cudaMemcpyHostToDevice, st), "opt upload");
     OPT_CK(cudaMemsetAsync(d + o_hist, 0, 8ull * nbins, st), "opt bins");
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    cudaEvent_t* ev = evs.e;
     if (ms) {
         OPT_CK(cudaEventCreate(&ev[0]), "event");
         OPT_CK(cudaEventCreate(&ev[1]), "event");
@@ -164,11 +171,7 @@ thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_of
                "opt overflow flags");
     }
     OPT_CK(cudaStreamSynchronize(st), "opt profiling");
-    if (ms) {
-        cudaEventElapsedTime(ms, ev[0], ev[1]);
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-    }
+    if (ms) OPT_CK(cudaEventElapsedTime(ms, ev[0], ev[1]), "profiling time");
     // the first count from the top whose suffix holds K rows
     for (uint32_t q = 0; q < nq; ++q) {
         const uint32_t n = id_off[q + 1] - id_off[q];
