@@ -19,7 +19,7 @@ Writes (to --out): selector_weights.json (parameters, normalisation, rule
 coefficients), selector_eval.json (the comparison) and selector_heldout.npz
 (held-out features and measured times).
 
-    python -m paper_1402_4466_gb300.train_selector --out gpurun_out
+    python -m paper_1402_4466_gb300.train_selector --out selector_out
 """
 from __future__ import annotations
 
@@ -167,7 +167,7 @@ def totals(times, choice):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", default="gpurun_out")
+    ap.add_argument("--out", default="selector_out")
     ap.add_argument("--train", type=int, default=50_000)
     ap.add_argument("--test", type=int, default=5_000)
     ap.add_argument("--reps", type=int, default=5)
