@@ -196,11 +196,7 @@ void form_groups(const BatchInput& in, uint32_t q0, uint32_t Q, std::vector<QDes
             const uint32_t T = qd[q0 + m].T;
             tlo = std::min(tlo, T);
             thi = std::max(thi, T);
-            if (T >= 1 && T <= n) {
-                int b = 0;
-                for (uint64_t v = T; v; v >>= 1) ++b;
-                need = std::max(need, b);
-            }
+            if (T >= 1 && T <= n) need = std::max(need, slices_for(T));
         }
         int c = -1;
         for (int w = 0; w < cnt; ++w)
@@ -261,10 +257,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         const uint32_t hi = (in.hi && sym == kSymRange) ? in.hi[q] : 0u;
         if (sym == kSymThreshold) {
             resolve_variant(n, in.T[q], in.variant ? in.variant[q] : kVarCsa, &cls, &z);
-        } else {  // ranges and parity: carry-save counting ones, 2^S > min(hi, n) + 1
+        } else {  // ranges and parity: carry-save counting ones, 2^S >= min(hi, n) + 1
             const uint64_t top = sym == kSymRange ? std::min<uint64_t>(hi, n) + 1 : 1;
-            int need = 0;
-            for (uint64_t v = top; v; v >>= 1) ++need;
+            const int need = slices_for(top);
             int cnt = 0;
             const KernelEntry* tab = kernel_table(&cnt);
             cls = cnt - 1;

@@ -259,8 +259,11 @@ struct Counters {
             sticky[h] = lop3<kOr3>(sticky[h], cy, src[(S * 8 + h) * 32 + lane]);
         }
     }
-    // bit-sliced "count >= thr" (thr < 2^S), most significant slice first
+    // bit-sliced "count >= thr" (thr <= 2^S), most significant slice first;
+    // the slices hold the count mod 2^S and the sticky slice "count >= 2^S",
+    // so thr = 2^S is the sticky slice alone
     __device__ __forceinline__ uint32_t ge(int h, uint32_t thr) const {
+        if (thr >> S) return sticky[h];
         uint32_t eq = ~0u, gt = 0u;
 #pragma unroll
         for (int k = S - 1; k >= 0; --k) {

@@ -20,6 +20,14 @@ int bits_of(uint64_t v) {
     return n;
 }
 
+}  // namespace
+
+// The fewest counter slices (at least 1) that decide "count >= t": 2^S >= t
+// (t = 2^S is decided by the sticky slice alone).
+int slices_for(uint64_t t) { return t <= 2 ? 1 : bits_of(t - 1); }
+
+namespace {
+
 cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t st) {
     if (cls == kClassScanCount) return launch_scancount(p, grid, st);
     if (class_family(cls) == 4)
@@ -72,7 +80,7 @@ void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode) {
     uint32_t z = 0;
     int need = 1;
     if (T >= 1 && T <= n) {  // T = 0 and T > n never reach the counters
-        const int s1 = bits_of(T), s0 = bits_of(uint64_t(n) - T + 1);
+        const int s1 = slices_for(T), s0 = slices_for(uint64_t(n) - T + 1);
         z = s0 < s1 ? 1u : 0u;
         need = std::min(s1, s0);
     }
@@ -102,10 +110,10 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
         if (*cls < kSplitWidths) *cls += kClassSplit;
         return;
     }
-    if (v == kVarPos) {  // ones counting: the first width with 2^S > T
+    if (v == kVarPos) {  // ones counting: the first width with 2^S >= T
         int cnt = 0;
         const KernelEntry* tab = kernel_table(&cnt);
-        const int need = (T >= 1 && T <= n) ? bits_of(T) : 1;
+        const int need = (T >= 1 && T <= n) ? slices_for(T) : 1;
         int c = cnt - 1;
         for (int i = 0; i < cnt; ++i)
             if (tab[i].S >= need) {

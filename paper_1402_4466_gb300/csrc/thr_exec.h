@@ -117,8 +117,10 @@ constexpr int kVarLooped = 4;
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 
 // Counter width and zero counting for a query of n inputs and threshold T:
-// counting ones needs 2^S > T, counting the zeros of the active inputs
-// 2^S > n - T + 1; the class is the first instantiated width that fits.
+// counting ones needs 2^S >= T, counting the zeros of the active inputs
+// 2^S >= n - T + 1 (a threshold of exactly 2^S is the sticky slice); the
+// class is the first instantiated width that fits.
+int slices_for(uint64_t t);  // the fewest S >= 1 with 2^S >= t
 void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode);
 
 // CTAs per SM of a class's kernel at full occupancy.

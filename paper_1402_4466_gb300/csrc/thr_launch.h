@@ -30,7 +30,7 @@ cudaError_t launch_looped(int M, const PassAParams&, int grid, cudaStream_t);
 cudaError_t occupancy_looped(int M, int* blocks_per_sm);
 
 // Instantiated counter widths, ascending; a query uses the first S with
-// 2^S > the largest threshold its counters test.
+// 2^S >= the largest threshold its counters test.
 const KernelEntry* kernel_table(int* count);
 
 #define THR_DECLARE_WIDTH(S)                                                 \
