@@ -446,7 +446,16 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     sig = fnv(sig, reinterpret_cast<uintptr_t>(pin));
     sig = fnv(sig, reinterpret_cast<uintptr_t>(dpool));
     sig = fnv(sig, cap);
-    sig = fnv(sig, reinterpret_cast<uintptr_t>(idx));
+    // the index's arrays the kernels read (another index may reuse the same
+    // host object address, or the same device addresses with its own data)
+    for (const void* ptr : {static_cast<const void*>(idx), static_cast<const void*>(idx->d_words),
+                            static_cast<const void*>(idx->d_sdesc),
+                            static_cast<const void*>(idx->d_pcls),
+                            static_cast<const void*>(idx->d_masks),
+                            static_cast<const void*>(idx->d_desc)})
+        sig = fnv(sig, reinterpret_cast<uintptr_t>(ptr));
+    sig = fnv(sig, uint64_t(idx->W) << 32 | idx->NG);
+    sig = fnv(sig, idx->r);
     for (const Launch& L : launches) {
         sig = fnv(sig, uint64_t(uint32_t(L.cls)) << 32 | L.list_off);
         sig = fnv(sig, uint64_t(L.nlist) << 32 | uint64_t(uint32_t(L.grid)));

@@ -150,6 +150,35 @@ def test_identical_plans_relaunch_the_cached_graph(mixed):
     assert thr.thr_last_batch_info()["graph"] == 1
 
 
+def test_relaunch_never_reuses_another_index():
+    """Two indexes of the same shape queried alternately with batches of the
+    same shape into the same device pool, then one freed and a new one built
+    in its place: every result is that of the index it was asked of."""
+    import torch
+    r = 3 * 8192 + 1000
+    pairs = []
+    for seed in (41, 42, 43):
+        arrays = [synth.bernoulli(seed, i, r, 0.05 + 0.02 * i) for i in range(12)]
+        gw, goff = thr.encode_many(arrays, r)
+        pairs.append((thr.idx_build_rle(gw, goff, r),
+                      oracle.Index([oracle.encode(a, r) for a in arrays], r)))
+    qs = [(np.arange(12, dtype=np.uint32), T) for T in (2, 3)]
+    pool = torch.zeros(2 * (pairs[0][0].nwords + 1), dtype=torch.int64, device="cuda")
+
+    def check(g, o):
+        off, ln, _ = thr.thr_query_batch(g, qs, pool=pool)
+        host = pool.cpu().numpy().view(np.uint64)
+        for k, (ids, T) in enumerate(qs):
+            assert np.array_equal(host[int(off[k]): int(off[k] + ln[k])], o.threshold(ids, T))
+    for g, o in (pairs[0], pairs[1], pairs[0], pairs[1]):
+        check(g, o)
+    pairs[0][0].close()
+    check(*pairs[2])
+    check(*pairs[1])
+    pairs[1][0].close()
+    pairs[2][0].close()
+
+
 def test_batch_many_inputs_per_query(mixed):
     """n above one chunk of input records (128) and above the ScanCount
     limit (255): the uncached id path and the carry-save fallback."""
