@@ -342,9 +342,9 @@ def run_ours(args):
     clk = clocks.stop()
 
     # end to end through the C ABI: host ids in, host result pool out (the
-    # pool is an ordinary host array allocated once and reused, as a caller
-    # would; its pages are touched before timing)
-    host_pool = np.zeros(len(Ts) * (W + 1), dtype=np.uint64)
+    # pool is page-locked host memory allocated once and reused, as a caller
+    # streaming results would; its pages are touched before timing)
+    host_pool = torch.zeros(len(Ts) * (W + 1), dtype=torch.int64, pin_memory=True)
     thr.thr_query_batch(idx, qs, pool=host_pool, flags=POLICY, stream=stream)
     e2e_ms, d2h = [], 0
     for _ in range(args.steps):

@@ -786,14 +786,15 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
 
 // Pass A with the carry-save counters (S-bit saturating bit slices); kPos
 // selects the position-major decode of mixed inputs.  Occupancy bounds
-// (measured on the many-criteria queries): 5 CTAs per SM up to S = 3 (96
-// registers, nearly no spills: 2-7% faster at T = 2..4 than 6 CTAs with 80
+// (measured on the many-criteria queries): 5 CTAs per SM up to S = 4 (96
+// registers, few spills: 2-7% faster at T = 2..4 than 6 CTAs with 80
 // registers, which in turn beat 8 CTAs with 64 by 7% for the grouped decode
-// and 28% for the position-major one), 4 up to S = 6, 3 up to S = 8 (the
+// and 28% for the position-major one; 4% faster at T = 16 than 4 CTAs with
+// 126 registers), 4 up to S = 6, 3 up to S = 8 (the
 // group members of wider counters finish out of line to stay within it),
 // 2 beyond.
 template <int S, bool kPos>
-__global__ void __launch_bounds__(kNT, (S <= 3 ? 5 : (S <= 6 ? 4 : (S <= 8 ? 3 : 2))))
+__global__ void __launch_bounds__(kNT, (S <= 4 ? 5 : (S <= 6 ? 4 : (S <= 8 ? 3 : 2))))
     k_threshold(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem& sm = *reinterpret_cast<CtaSmem*>(smem_raw);
