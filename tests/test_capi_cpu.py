@@ -128,3 +128,28 @@ def test_encode_rows_matches_word_encoders():
         thr.thr_rle_encode_rows([9, 5], 100)
     with pytest.raises(thr.ThrError):
         thr.thr_rle_encode_rows([100], 100)
+
+
+def test_rule_model_coefficients_round_trip():
+    """The rule chooser's 12 coefficients (host state): set, read back, and
+    the shipped ones restored; no GPU involved."""
+    from paper_1402_4466_gb300 import selector_weights
+    shipped = selector_weights.load()["rule_coefficients"]
+    before = thr.rule_model()
+    try:
+        c = np.arange(1, 13, dtype=np.float64) * 0.5
+        assert np.array_equal(thr.rule_model(c), c)
+        assert np.array_equal(thr.rule_model(), c)
+        assert np.array_equal(thr.rule_model(shipped), np.asarray(shipped, np.float64))
+    finally:
+        thr.rule_model(before)
+
+
+def test_shipped_selector_weights_fit_the_library():
+    """The shipped model has the library's parameter count and a 12-term rule."""
+    from paper_1402_4466_gb300 import selector_weights
+    d = selector_weights.load()
+    assert len(d["params"]) == thr.SEL_PARAMS
+    assert len(d["mean"]) == 16 and len(d["istd"]) == 16
+    assert len(d["rule_coefficients"]) == 12
+    assert all(np.isfinite(d["params"])) and all(v > 0 for v in d["istd"])
