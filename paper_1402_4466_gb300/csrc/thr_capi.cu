@@ -300,18 +300,21 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
     for (uint32_t b = 0; b < nbitmaps; ++b)
         if (rcs[b]) return fail(THR_E_FORMAT, "bitmap %u: %s", b, whys[b].c_str());
 
-    thr_index* idx = new (std::nothrow) thr_index;
-    if (!idx) return fail(THR_E_NOMEM, "host allocation");
-    CK(cudaGetDevice(&idx->device), "cudaGetDevice");
+    int device = 0, num_sms = 0;
+    CK(cudaGetDevice(&device), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device),
+       "device attributes");
     {  // keep query scratch in the device's stream-ordered pool between queries
         cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, idx->device) == cudaSuccess) {
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
             uint64_t keep = ~0ull;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         }
     }
-    CK(cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device),
-       "device attributes");
+    thr_index* idx = new (std::nothrow) thr_index;
+    if (!idx) return fail(THR_E_NOMEM, "host allocation");
+    idx->device = device;
+    idx->num_sms = num_sms;
     idx->nbitmaps = nbitmaps;
     idx->r = r;
     idx->W = uint32_t(W);
