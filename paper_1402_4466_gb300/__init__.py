@@ -24,6 +24,7 @@ THR_OK, THR_E_INVAL, THR_E_FORMAT, THR_E_NOMEM = 0, 1, 2, 3
 THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT = 4, 5, 6
 THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
+THR_POLICY_MASK = 0xF0
 THR_PROFILE = 0x100
 THR_NO_GRAPH = 0x1000
 THR_NO_SHARE = 0x2000
@@ -31,6 +32,7 @@ THR_SYM_ODD = 0x4000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 THR_VARIANT_SPLIT = 0x600
 THR_VARIANT_LOOPED = 0x800
+THR_VARIANT_MASK = 0xE00
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",

@@ -153,3 +153,21 @@ def test_shipped_selector_weights_fit_the_library():
     assert len(d["mean"]) == 16 and len(d["istd"]) == 16
     assert len(d["rule_coefficients"]) == 12
     assert all(np.isfinite(d["params"])) and all(v > 0 for v in d["istd"])
+
+
+def test_binding_constants_match_the_header():
+    """Every flag, status and size constant of include/thr.h has the same
+    value in the Python binding (the binding restates them for ctypes)."""
+    text = open(HEADER).read()
+    defines = {m.group(1): int(m.group(2), 0) for m in
+               re.finditer(r"^#define (THR_[A-Z0-9_]+) (0x[0-9A-Fa-f]+|[0-9]+)u?", text, flags=re.M)}
+    enums = {m.group(1): int(m.group(2)) for m in
+             re.finditer(r"^\s*(THR_(?:OK|E_[A-Z]+)) = ([0-9]+)", text, flags=re.M)}
+    assert len(defines) >= 18 and len(enums) == 7
+    sel = {"THR_SEL_FEATURES": thr.SEL_FEATURES, "THR_SEL_VARIANTS": thr.SEL_VARIANTS,
+           "THR_SEL_PARAMS": thr.SEL_PARAMS}
+    for name, value in {**defines, **enums}.items():
+        if name in sel:
+            assert sel[name] == value, name
+        else:
+            assert getattr(thr, name) == value, name
