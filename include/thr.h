@@ -225,7 +225,7 @@ thr_status thr_query_batch(const thr_index *idx, uint32_t nq,
  * by another allocator that reserved the device up front, or code that must
  * not risk an allocation failure, or the device synchronisation an
  * allocation or free can cause, in the middle of its work.  Every scratch
- * buffer the kernels need lives in one fixed device array of about 8.75 MiB
+ * buffer the kernels need lives in one fixed device array of about 9.25 MiB
  * inside the library, which each GPU that loads the library holds until the
  * process exits; the call allocates nothing (no cudaMalloc, stream-ordered
  * or pinned allocation).
