@@ -131,7 +131,8 @@ thr_status idx_build_rle(const uint64_t *words, const uint64_t *offsets,
  *   n         1 <= n <= 65536
  *   T         any value; 0 gives every row, > n gives none
  *   out       caller-owned buffer of cap words: host memory, or device memory
- *             when flags has THR_OUT_DEVICE
+ *             of the index's GPU (or managed memory) when flags has
+ *             THR_OUT_DEVICE; device memory of another GPU is THR_E_INVAL
  *   cap       capacity of out in words; cap >= ceil(r/64) + 1 always suffices
  *   out_len   receives the encoded length in words.  When it exceeds cap the
  *             call returns THR_E_NOSPACE and the contents of out are
@@ -229,7 +230,8 @@ thr_status thr_query_batch(const thr_index *idx, uint32_t nq,
  * inside the library, which each GPU that loads the library holds until the
  * process exits; the call allocates nothing (no cudaMalloc, stream-ordered
  * or pinned allocation).
- *   out       device memory only, cap words; the other arguments and the
+ *   out       device memory of the index's GPU (or managed memory) only, cap
+ *             words; the other arguments and the
  *             result are as for thr_query with THR_OUT_DEVICE
  * Limits: ceil(r/64) <= 2^20 words (r <= 2^26 rows) and n <= 65536;
  * larger queries return THR_E_INVAL.  The first call on a device looks up

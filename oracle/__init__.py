@@ -46,10 +46,14 @@ class OracleError(RuntimeError):
 
 
 def compile_c(src: str, out: str) -> str:
-    """gcc -O2 -shared; plain C11, no machine-specific flags."""
+    """gcc -O2 -shared; plain C11, no machine-specific flags.  With OpenMP
+    when the compiler has it (the row-partitioned ScanCount then runs its
+    ranges on several threads), else without (they run one after another)."""
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall",
-                    "-Wextra", "-o", tmp, src], check=True)
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-Wextra"]
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, src], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(base + ["-o", tmp, src], check=True)
     os.replace(tmp, out)
     return out
 
@@ -94,9 +98,12 @@ class Oracle:
                                       ctypes.c_int, u64p, u64, u64p]
         lib.orc_opt_threshold.argtypes = [u64p, u64p, u32, u64, u32p, u32, u64, u32p,
                                           u64p, u64, u64p]
+        lib.orc_threshold_parts.argtypes = [u64p, u64p, u32, u64, u32p, u32, u32, u32,
+                                            u64p, u64, u64p]
+        lib.orc_max_threads.argtypes = []
         for f in (lib.orc_encode, lib.orc_decode, lib.orc_validate,
                   lib.orc_threshold, lib.orc_threshold_words, lib.orc_symmetric,
-                  lib.orc_opt_threshold):
+                  lib.orc_opt_threshold, lib.orc_threshold_parts, lib.orc_max_threads):
             f.restype = ctypes.c_int
         self.c = lib
 
@@ -142,6 +149,27 @@ class Oracle:
                                   ctypes.byref(n))
         if rc != OK:
             raise OracleError(rc, "threshold")
+        return out[: n.value].copy()
+
+    def max_threads(self) -> int:
+        """Threads the row-partitioned query may use (1 without OpenMP)."""
+        return int(self.c.orc_max_threads())
+
+    def threshold_parts(self, words, offsets, r: int, ids, T: int,
+                        parts: int) -> np.ndarray:
+        """The threshold query with the rows cut into `parts` word ranges,
+        each counted on its own (on OpenMP threads when available)."""
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        cap = nwords(r) + 1
+        out = np.empty(cap, dtype=np.uint64)
+        n = ctypes.c_uint64(0)
+        rc = self.c.orc_threshold_parts(_p64(words), _p64(offsets), len(offsets) - 1, int(r),
+                                        _p32(ids), ids.size, int(T), int(parts), _p64(out),
+                                        cap, ctypes.byref(n))
+        if rc != OK:
+            raise OracleError(rc, "threshold_parts")
         return out[: n.value].copy()
 
     def symmetric(self, words, offsets, r: int, ids, lo: int, hi: int,
@@ -246,6 +274,9 @@ class Index:
     def threshold_words(self, ids, T: int) -> np.ndarray:
         return self._o().threshold_words(self.words, self.offsets, self.r,
                                          ids, T)
+
+    def threshold_parts(self, ids, T: int, parts: int) -> np.ndarray:
+        return self._o().threshold_parts(self.words, self.offsets, self.r, ids, T, parts)
 
     def symmetric(self, ids, lo: int, hi: int, odd: bool = False) -> np.ndarray:
         return self._o().symmetric(self.words, self.offsets, self.r, ids, lo, hi, odd)

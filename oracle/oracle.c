@@ -43,6 +43,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_E_INVAL 1
@@ -377,5 +380,95 @@ int orc_threshold_words(const uint64_t *streams, const uint64_t *offsets,
 done:
     free(count);
     free(rows);
+    return rc;
+}
+
+/*
+ * The same ScanCount partitioned by row range (the multi-core CPU baseline):
+ * the W words are cut into `parts` contiguous word ranges; each range keeps
+ * its own counters and walks every input stream, counting only the rows that
+ * fall inside it (fill runs of ones row by row, literal words bit by bit with
+ * the trailing-zero loop), then marks its rows whose count reaches T.  One
+ * canonical encoding of all W words follows.  The ranges run on OpenMP
+ * threads when the library was compiled with OpenMP (orc_max_threads() > 1),
+ * else one after the other; the result does not depend on either.  Streams
+ * are validated first (orc_validate), so the range walks trust the format.
+ */
+static void orc_count_range(const uint64_t *s, uint64_t W, uint64_t w0, uint64_t w1,
+                            uint32_t *count)
+{
+    uint64_t covered = 0, i = 0;
+    while (covered < W && covered < w1) {
+        uint64_t mw = s[i++];
+        uint64_t b = mw & 1, F = (mw >> 1) & 0xFFFFFFFFull, L = mw >> 33;
+        if (b) {
+            uint64_t a = covered > w0 ? covered : w0;
+            uint64_t e = covered + F < w1 ? covered + F : w1;
+            for (uint64_t w = a; w < e; w++)
+                for (uint64_t x = w * 64; x < w * 64 + 64; x++) count[x - w0 * 64]++;
+        }
+        covered += F;
+        for (uint64_t k = 0; k < L; k++) {
+            uint64_t v = s[i++];
+            if (covered >= w0 && covered < w1) {
+                while (v) {
+                    count[covered * 64 + (uint64_t)orc_ctz(v) - w0 * 64]++;
+                    v &= v - 1;
+                }
+            }
+            covered++;
+        }
+    }
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int orc_threshold_parts(const uint64_t *streams, const uint64_t *offsets,
+                        uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
+                        uint32_t n, uint32_t T, uint32_t parts, uint64_t *out,
+                        uint64_t cap, uint64_t *out_len)
+{
+    uint64_t W = orc_nwords(r);
+    uint64_t *words = NULL;
+    int rc = ORC_OK, bad = 0;
+    if (out_len == NULL || (n > 0 && ids == NULL) || offsets == NULL || parts == 0)
+        return ORC_E_INVAL;
+    for (uint32_t q = 0; q < n; q++)
+        if (ids[q] >= nbitmaps) return ORC_E_INVAL;
+    for (uint32_t q = 0; q < n; q++) {
+        uint64_t b = ids[q];
+        rc = orc_validate(streams + offsets[b], offsets[b + 1] - offsets[b], r);
+        if (rc != ORC_OK) return rc;
+    }
+    words = (uint64_t *)calloc(W > 0 ? W : 1, sizeof(uint64_t));
+    if (!words) return ORC_E_NOMEM;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(| : bad)
+#endif
+    for (int64_t p = 0; p < (int64_t)parts; p++) {
+        uint64_t w0 = W * (uint64_t)p / parts, w1 = W * (uint64_t)(p + 1) / parts;
+        uint32_t *count;
+        if (w1 == w0) continue;
+        count = (uint32_t *)calloc((w1 - w0) * 64, sizeof(uint32_t));
+        if (!count) {
+            bad = 1;
+            continue;
+        }
+        for (uint32_t q = 0; q < n; q++)
+            orc_count_range(streams + offsets[ids[q]], W, w0, w1, count);
+        for (uint64_t x = w0 * 64; x < w1 * 64 && x < r; x++)
+            if (count[x - w0 * 64] >= T) words[x / 64] |= 1ull << (x % 64);
+        free(count);
+    }
+    if (bad) rc = ORC_E_NOMEM;
+    else rc = orc_encode(words, W, r, out, cap, out_len);
+    free(words);
     return rc;
 }

@@ -13,9 +13,9 @@ inputs resident in HBM, results into a device pool):
   batched   the 4096 queries in one thr_query_batch call (CUDA graph, launch
             configuration from the autotuner), with the plain, rule and
             learned variant policies
-Checked: every batched result equals the plain one (word for word), every
-result contains its query's prototype row, and a few sampled queries equal
-the CPU oracle's result.
+Checked: every sampled batched result equals the plain one (word for
+word) and contains its query's prototype row.  (The comparison with the CPU
+oracle at this workload's shape is a GPU test, tests/test_gpu_configs.py.)
 
     python -m paper_1402_4466_gb300.batch_bench --out similarity.json
 """
@@ -43,7 +43,6 @@ def main():
     ap.add_argument("--log-r", type=int, default=24)
     ap.add_argument("--queries", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--oracle-samples", type=int, default=3)
     ap.add_argument("--pool", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
@@ -110,7 +109,7 @@ def main():
                          "variant_counts": np.bincount(variants, minlength=3).tolist()}
         print(json.dumps({name: results[name]}), flush=True)
 
-    # checks: batch == plain, prototype rows present, oracle samples
+    # checks: batch == plain, prototype rows present
     off, ln, _ = thr.thr_query_batch(idx, queries, pool=pool, stream=stream)
     host = pool.cpu().numpy().view(np.uint64)
     mismatches = 0
@@ -139,17 +138,6 @@ def main():
         else:
             bit = 0
         proto_missing += 0 if bit else 1
-    oracle_ok = None
-    if args.oracle_samples:
-        import oracle
-        rng = np.random.default_rng(0)
-        streams = [words[int(offsets[i]):int(offsets[i + 1])] for i in range(args.nb)]
-        o = oracle.Index(streams, r)
-        oracle_ok = 0
-        for k in rng.choice(len(queries), args.oracle_samples, replace=False).tolist():
-            ids, T = queries[k]
-            got = host[int(off[k]): int(off[k] + ln[k])]
-            oracle_ok += 1 if np.array_equal(got, o.threshold(ids, T)) else 0
     res = {
         "workload": f"similarity: {args.nb} term bitmaps x 2^{args.log_r} rows, densities "
                     f"min(0.3, C k^-1.1) summing to 110, {len(queries)} queries of N~U[10,200] "
@@ -163,8 +151,7 @@ def main():
         "batched": results,
         "autotune": {"best": tune_best, "ms": [round(x, 3) for x in tune_ms]},
         "checks": {"sampled": len(sampled), "batch_vs_plain_mismatches": mismatches,
-                   "prototype_rows_missing": proto_missing,
-                   "oracle_samples_equal": oracle_ok, "oracle_samples": args.oracle_samples},
+                   "prototype_rows_missing": proto_missing},
     }
     res["speedup_batched_learned_vs_plain"] = round(results["learned"]["qps"] /
                                                     res["plain"]["qps"], 3)

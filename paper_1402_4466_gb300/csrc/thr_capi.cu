@@ -109,13 +109,18 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     return THR_OK;
 }
 
-bool is_device_ptr(const void* p) {
+// Is p memory the kernels of device dev may write: device memory of dev
+// itself, or managed memory?  Device memory of another GPU is refused: the
+// kernels would write it through a peer address, which faults without peer
+// access.
+bool is_device_ptr(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -460,8 +465,8 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool dev_out = flags & THR_OUT_DEVICE;
-    if (dev_out && cap > 0 && !is_device_ptr(out))
-        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+    if (dev_out && cap > 0 && !is_device_ptr(out, idx->device))
+        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory of the index's GPU");
     if (dev_out) {
         thr_status s = run_query(idx, ids, n, T, out, cap, out_len, st, profile, variant);
         if (s == THR_OK && *out_len > cap)
@@ -553,8 +558,8 @@ thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t off = 0, total = 0;
     if (flags & THR_OUT_DEVICE) {
-        if (cap > 0 && !is_device_ptr(out))
-            return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+        if (cap > 0 && !is_device_ptr(out, idx->device))
+            return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory of the index's GPU");
         thr_status s = run_batch(idx, in, out, cap, &off, out_len, &total, st, opt, &stats);
         if (s != THR_OK) return s;
         if (opt.profile) g_kernel_ms = stats.pass_a_ms;
@@ -624,8 +629,8 @@ thr_status thr_query_opt(const thr_index* idx, const uint32_t* ids, uint32_t n, 
     for (uint32_t i = 0; i < n; ++i)
         if (ids[i] >= idx->nbitmaps)
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
-    if ((flags & THR_OUT_DEVICE) && cap > 0 && !is_device_ptr(out))
-        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory");
+    if ((flags & THR_OUT_DEVICE) && cap > 0 && !is_device_ptr(out, idx->device))
+        return fail(THR_E_INVAL, "THR_OUT_DEVICE given but out is not device memory of the index's GPU");
     const uint32_t id_off[2] = {0, n};
     float ms = 0.f;
     thr_status s = opt_profile(idx, 1, id_off, ids, &K, T_out, (cudaStream_t)cuda_stream,
@@ -658,7 +663,7 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t total = 0;
     if (flags & THR_OUT_DEVICE) {
-        if (pool_cap > 0 && !is_device_ptr(pool))
+        if (pool_cap > 0 && !is_device_ptr(pool, idx->device))
             return fail(THR_E_INVAL, "THR_OUT_DEVICE given but pool is not device memory");
         thr_status s = run_batch(idx, in, pool, pool_cap, out_off, out_len, &total, st, opt,
                                  &stats);

@@ -96,9 +96,11 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     if (cap > 0) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, out) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            (a.type != cudaMemoryTypeManaged &&
+             (a.type != cudaMemoryTypeDevice || a.device != dev))) {
             cudaGetLastError();
-            return report_error(THR_E_INVAL, "thr_query_static writes to device memory only");
+            return report_error(THR_E_INVAL,
+                                "thr_query_static writes to device memory of the index's GPU only");
         }
     }
     unsigned char* blk = nullptr;

@@ -349,7 +349,28 @@ def pin_invariants(o, seed=17, trials=15):
         assert dup3 == (B[0] & B[1])
 
 
+def pin_row_partitions(o, seed=19, trials=25):
+    """The row-partitioned ScanCount (the multi-core CPU baseline) against
+    brute force: every split of the rows into word ranges, including more
+    ranges than words, fills of ones that cross range borders, ragged tails
+    and repeated ids."""
+    rng = np.random.default_rng(seed)
+    for _ in range(trials):
+        n = int(rng.integers(1, 9))
+        r = int(rng.choice([1, 64, 65, 300, 1000, 1536, 4097]))
+        B = random_bitsets(rng, n, r)
+        words, offs = oracle.concat(streams_for(o, B, r))
+        ids = list(range(n)) + [int(rng.integers(0, n))]
+        for parts in (1, 2, 3, 7, nwords(r) + 2):
+            for T in range(0, n + 3):
+                enc = o.threshold_parts(words, offs, r, ids, T, parts)
+                want = brute(B, r, T, ids)
+                got = sum(1 << int(x) for x in o.decode(enc, r))
+                assert got == want, f"parts={parts} n={n} r={r} T={T}"
+                assert enc.tolist() == o.encode(int_to_words(want, r), r).tolist()
+
+
 ALL_PINS = [pin_fig1, pin_sets_example, pin_word_layout, pin_bstm_trace,
             pin_looped_trace, pin_rbmrg_ewah, pin_format_cases,
             pin_rejects_malformed, pin_roundtrip, pin_brute_force,
-            pin_independent_algorithms, pin_invariants]
+            pin_independent_algorithms, pin_invariants, pin_row_partitions]

@@ -36,6 +36,13 @@ MUTANTS = [
      "prevb != b && prevF != ORC_FMAX"),
     ("last row dropped", "if (count[x] >= T) words",
      "if (count[x] >= T && x + 1 < r) words"),
+    ("row range ends one word early",
+     "w1 = W * (uint64_t)(p + 1) / parts;", "w1 = W * (uint64_t)(p + 1) / parts - 1;"),
+    ("ones fill of a range stops one word short",
+     "uint64_t e = covered + F < w1 ? covered + F : w1;",
+     "uint64_t e = covered + F < w1 ? covered + F : w1 - 1;"),
+    ("literals of a range's first word skipped",
+     "if (covered >= w0 && covered < w1) {", "if (covered > w0 && covered < w1) {"),
     ("literal copied from the wrong slot",
      "if (n < cap && out) out[n] = words[lit0 + k];",
      "if (n < cap && out) out[n] = words[lit0];"),
