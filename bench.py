@@ -51,7 +51,7 @@ METRIC = ("threshold queries/s and compressed-input GB/s (bit-exact) vs HBM peak
           "batched+learned vs plain")
 WORKLOAD = ("many-criteria: 64 bitmaps x 2^26 rows, densities log-uniform [1e-4, 0.3], "
             "half i.i.d., half clustered (mean run 256 rows); one step = T in {2,16,32,63}")
-KERNEL_SOURCES = ("thr_device.cuh", "thr_query_kernel.cuh")
+KERNEL_SOURCES = ("thr_device.cuh", "thr_query_kernel.cuh", "thr_staged.cuh")
 
 
 def parse():
@@ -66,7 +66,7 @@ def parse():
                     help="build the workload, run one warm-up query at threshold T and "
                          "then one more (the launch to capture with a profiler); no timing")
     ap.add_argument("--variant", default="csa",
-                    choices=["csa", "position", "scancount", "looped"],
+                    choices=["csa", "direct", "position", "scancount", "looped"],
                     help="counting variant of --profile-query")
     ap.add_argument("--batch", action="store_true",
                     help="with --profile-query: the step's four thresholds as one batched "
@@ -305,7 +305,8 @@ def run_ours(args):
     plain_value = len(q_ms) / (sum(q_ms) / 1e3)
     plain_results = {T: thr.thr_query(idx, ids, T) for T in Ts}
     variant_ms = {}
-    for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("position", thr.THR_VARIANT_POSITION),
+    for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("direct", thr.THR_VARIANT_DIRECT),
+                         ("position", thr.THR_VARIANT_POSITION),
                          ("scancount", thr.THR_VARIANT_SCANCOUNT)):
         per_t = {}
         for T in Ts:
@@ -587,7 +588,8 @@ def profile_query(args):
     torch.cuda.init()
     r, gw, goff = make_index_inputs(args.seed)
     idx = thr.idx_build_rle(gw, goff, r)
-    flag = {"csa": thr.THR_VARIANT_CSA, "position": thr.THR_VARIANT_POSITION,
+    flag = {"csa": thr.THR_VARIANT_CSA, "direct": thr.THR_VARIANT_DIRECT,
+            "position": thr.THR_VARIANT_POSITION,
             "scancount": thr.THR_VARIANT_SCANCOUNT, "looped": thr.THR_VARIANT_LOOPED}[args.variant]
     ids = np.arange(synth.MANY_N, dtype=np.uint32)
     dout = torch.empty(idx.nwords + 1, dtype=torch.int64, device="cuda")

@@ -36,8 +36,10 @@
  * Errors: every call returns a thr_status; no C++ exception crosses the ABI.
  * thr_last_error() describes the last failure of the calling thread.
  * A CUDA failure returns THR_E_CUDA.  No kernel of the library waits on
- * another CTA or launch (cross-CTA scans finish in the last CTA to arrive),
- * so THR_E_TIMEOUT is reserved and not returned.
+ * another CTA or launch (cross-CTA scans finish in the last CTA to arrive).
+ * The one device-side wait is a warp's wait for its own bulk copies into
+ * shared memory (THR_VARIANT_CSA); it gives up after about a second, and the
+ * call then returns THR_E_TIMEOUT (the results are not valid).
  */
 #ifndef THR_H
 #define THR_H
@@ -57,7 +59,7 @@ typedef enum {
     THR_E_NOMEM = 3,   /* host or device allocation failed */
     THR_E_NOSPACE = 4, /* output buffer too small; required size returned */
     THR_E_CUDA = 5,    /* a CUDA runtime call failed */
-    THR_E_TIMEOUT = 6  /* reserved (no device-side waits) */
+    THR_E_TIMEOUT = 6  /* a kernel gave up waiting for its shared-memory copies */
 } thr_status;
 
 /* flags for thr_query / thr_query_batch */
@@ -76,7 +78,10 @@ typedef enum {
  *                          (default; any n and T), inputs decoded four at a
  *                          time; when T is close to n the zeros of the
  *                          active inputs are counted instead, which needs
- *                          fewer counter bits
+ *                          fewer counter bits.  Each input's compressed
+ *                          words for a 128-word subtile are first copied to
+ *                          shared memory by bulk copies, several inputs
+ *                          ahead of the adds
  *   THR_VARIANT_POSITION   the same counters counting ones; inputs that mix
  *                          fills and literals inside a 128-word subtile are
  *                          decoded position by position (each lane walks the
@@ -94,12 +99,16 @@ typedef enum {
  *                          per word, C_j = rows counted at least j times so
  *                          far, each input one AND-OR per level; used when
  *                          1 <= T <= 4 and T <= n, else CSA runs.  Not an arm
- *                          of the rule or learned policies. */
+ *                          of the rule or learned policies.
+ *   THR_VARIANT_DIRECT     THR_VARIANT_CSA without the shared-memory copies:
+ *                          every word is loaded from global memory where it
+ *                          is added (for comparison; not a policy arm) */
 #define THR_VARIANT_CSA 0x000u
 #define THR_VARIANT_SCANCOUNT 0x200u
 #define THR_VARIANT_POSITION 0x400u
 #define THR_VARIANT_SPLIT 0x600u
 #define THR_VARIANT_LOOPED 0x800u
+#define THR_VARIANT_DIRECT 0xA00u
 #define THR_VARIANT_MASK 0xE00u
 
 /*

@@ -429,7 +429,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         e = cudaMemcpyAsync(h_res, b.scratch + lay.res, 16 * size_t(nq), cudaMemcpyDeviceToHost,
                             s);
         if (e != cudaSuccess) return e;
-        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, 8,
+        // the running output total and the kernels' error word
+        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, 16,
                                cudaMemcpyDeviceToHost, s);
     };
 
@@ -438,7 +439,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     // of a cached executable, it is launched as it is (its copy of the plan
     // reads the pinned staging, which holds this call's plan)
     uint64_t sig = fnv(key, plan_bytes);
-    for (size_t v : {o_ids, o_lists, o_grp, o_memb, lay.gtick, lay.base, lay.work, lay.tick,
+    for (size_t v : {o_ids, o_lists, o_grp, o_memb, lay.gtick, lay.base, lay.err, lay.work, lay.tick,
                      lay.res, lay.full, lay.bagg, lay.bpref, lay.aggs, lay.pref, lay.U, lay.total})
         sig = fnv(sig, v);
     sig = fnv(sig, nq);
@@ -452,10 +453,12 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                             static_cast<const void*>(idx->d_sdesc),
                             static_cast<const void*>(idx->d_pcls),
                             static_cast<const void*>(idx->d_masks),
+                            static_cast<const void*>(idx->d_sseg),
                             static_cast<const void*>(idx->d_desc)})
         sig = fnv(sig, reinterpret_cast<uintptr_t>(ptr));
     sig = fnv(sig, uint64_t(idx->W) << 32 | idx->NG);
     sig = fnv(sig, idx->r);
+    sig = fnv(sig, test_lost_copy());
     for (const Launch& L : launches) {
         sig = fnv(sig, uint64_t(uint32_t(L.cls)) << 32 | L.list_off);
         sig = fnv(sig, uint64_t(L.nlist) << 32 | uint64_t(uint32_t(L.grid)));
@@ -537,6 +540,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         }
         if (stats) stats->pass_a_ms = ms;
     }
+    if (h_res[2 * size_t(nq) + 1] & 0xFFFFFFFFull)
+        return report_error(THR_E_TIMEOUT,
+                            "a query kernel gave up waiting for its shared-memory copies");
     for (uint32_t q = 0; q < nq; ++q) {
         h_off[q] = h_res[2 * size_t(q)];
         h_len[q] = h_res[2 * size_t(q) + 1];

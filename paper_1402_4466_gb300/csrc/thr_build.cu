@@ -97,6 +97,7 @@ __global__ void k_subtile_class(const uint2* __restrict__ mtab,
                                 const uint32_t* __restrict__ ttab,
                                 const BitmapDesc* __restrict__ desc,
                                 uint64_t* __restrict__ sdesc,
+                                uint64_t* __restrict__ sseg,
                                 uint32_t* __restrict__ mixed_count, uint32_t W,
                                 uint32_t NG) {
     const uint32_t b = blockIdx.x;
@@ -167,7 +168,14 @@ __global__ void k_subtile_class(const uint2* __restrict__ mtab,
         }
         __syncthreads();
         const uint32_t rank = carry + warp_sum[wid] + incl - mixed;
-        if (g < NG) sdesc[uint64_t(b) * NG + g] = mixed ? (word | (uint64_t(rank) << 19)) : word;
+        if (g < NG) {
+            sdesc[uint64_t(b) * NG + g] = mixed ? (word | (uint64_t(rank) << 19)) : word;
+            // a literal run: its words are the segment (mixed: k_subtile_masks)
+            const uint64_t c = word & 3u;
+            sseg[uint64_t(b) * NG + g] =
+                c == 2 ? ((word >> 19) | (uint64_t(min(uint32_t(kGW), W - g * uint32_t(kGW))) << 32))
+                       : 0ull;
+        }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = rank + mixed;
         __syncthreads();
@@ -186,7 +194,7 @@ __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
                                 const uint32_t* __restrict__ ttab,
                                 const BitmapDesc* __restrict__ desc,
                                 const uint64_t* __restrict__ mixed_base,
-                                uint64_t* __restrict__ sdesc,
+                                uint64_t* __restrict__ sdesc, uint64_t* __restrict__ sseg,
                                 MaskRec* __restrict__ masks, uint32_t nbitmaps,
                                 uint32_t W, uint32_t NG) {
     const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -237,6 +245,10 @@ __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
     const uint64_t idx = mixed_base[b] + (sd >> 19);
     masks[idx] = rec;
     sdesc[i] = (sd & ((1ull << 19) - 1)) | (idx << 19);
+    // the stream words of the subtile's literals and group starts: from the
+    // first literal (base) on, `run` of them (at most kGW: each group start
+    // takes a fill word of the subtile, each literal a word)
+    sseg[i] = uint64_t(base) | (uint64_t(run) << 32);
 }
 
 // Thread per (bitmap, word): the classes of 32 consecutive subtiles.
@@ -264,7 +276,7 @@ cudaError_t launch_pack_classes(const uint64_t* sdesc, uint64_t* pcls, uint32_t 
 
 cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
                                  const BitmapDesc* desc, uint2* mtab, uint32_t* ttab,
-                                 uint64_t* sdesc, uint32_t* mixed_count,
+                                 uint64_t* sdesc, uint64_t* sseg, uint32_t* mixed_count,
                                  uint32_t nbitmaps, uint32_t W, uint32_t NG,
                                  cudaStream_t st) {
     k_marker_scan<<<nbitmaps, 256, 0, st>>>(words, mpos, desc, mtab, W);
@@ -273,17 +285,18 @@ cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
     const uint64_t n = (uint64_t(NG) + 1) * nbitmaps;
     k_tile_table<<<unsigned((n + 255) / 256), 256, 0, st>>>(mtab, desc, ttab, nbitmaps, NG);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_subtile_class<<<nbitmaps, 256, 0, st>>>(mtab, ttab, desc, sdesc, mixed_count, W, NG);
+    k_subtile_class<<<nbitmaps, 256, 0, st>>>(mtab, ttab, desc, sdesc, sseg, mixed_count, W,
+                                              NG);
     return cudaGetLastError();
 }
 
 cudaError_t launch_index_build_b(const uint2* mtab, const uint32_t* ttab,
                                  const BitmapDesc* desc, const uint64_t* mixed_base,
-                                 uint64_t* sdesc, MaskRec* masks, uint32_t nbitmaps,
-                                 uint32_t W, uint32_t NG, cudaStream_t st) {
+                                 uint64_t* sdesc, uint64_t* sseg, MaskRec* masks,
+                                 uint32_t nbitmaps, uint32_t W, uint32_t NG, cudaStream_t st) {
     const uint64_t ns = uint64_t(NG) * nbitmaps;
     k_subtile_masks<<<unsigned((ns + 255) / 256), 256, 0, st>>>(mtab, ttab, desc, mixed_base,
-                                                               sdesc, masks, nbitmaps, W, NG);
+                                                               sdesc, sseg, masks, nbitmaps, W, NG);
     return cudaGetLastError();
 }
 

@@ -130,27 +130,38 @@ thr_status report_error(thr_status st, const char* msg) { return fail(st, "%s", 
 
 const KernelEntry* kernel_table(int* count) {
     static const KernelEntry tab[] = {
-        {1, launch_threshold_1, occupancy_threshold_1, launch_threshold_pos_1,
+        {1, launch_staged_1, occupancy_staged_1, launch_threshold_1,
+         occupancy_threshold_1, launch_threshold_pos_1,
          occupancy_threshold_pos_1, launch_split_1, occupancy_split_1},
-        {2, launch_threshold_2, occupancy_threshold_2, launch_threshold_pos_2,
+        {2, launch_staged_2, occupancy_staged_2, launch_threshold_2,
+         occupancy_threshold_2, launch_threshold_pos_2,
          occupancy_threshold_pos_2, launch_split_2, occupancy_split_2},
-        {3, launch_threshold_3, occupancy_threshold_3, launch_threshold_pos_3,
+        {3, launch_staged_3, occupancy_staged_3, launch_threshold_3,
+         occupancy_threshold_3, launch_threshold_pos_3,
          occupancy_threshold_pos_3, launch_split_3, occupancy_split_3},
-        {4, launch_threshold_4, occupancy_threshold_4, launch_threshold_pos_4,
+        {4, launch_staged_4, occupancy_staged_4, launch_threshold_4,
+         occupancy_threshold_4, launch_threshold_pos_4,
          occupancy_threshold_pos_4, launch_split_4, occupancy_split_4},
-        {5, launch_threshold_5, occupancy_threshold_5, launch_threshold_pos_5,
+        {5, launch_staged_5, occupancy_staged_5, launch_threshold_5,
+         occupancy_threshold_5, launch_threshold_pos_5,
          occupancy_threshold_pos_5, launch_split_5, occupancy_split_5},
-        {6, launch_threshold_6, occupancy_threshold_6, launch_threshold_pos_6,
+        {6, launch_staged_6, occupancy_staged_6, launch_threshold_6,
+         occupancy_threshold_6, launch_threshold_pos_6,
          occupancy_threshold_pos_6, launch_split_6, occupancy_split_6},
-        {7, launch_threshold_7, occupancy_threshold_7, launch_threshold_pos_7,
+        {7, launch_staged_7, occupancy_staged_7, launch_threshold_7,
+         occupancy_threshold_7, launch_threshold_pos_7,
          occupancy_threshold_pos_7, launch_split_7, occupancy_split_7},
-        {8, launch_threshold_8, occupancy_threshold_8, launch_threshold_pos_8,
+        {8, launch_staged_8, occupancy_staged_8, launch_threshold_8,
+         occupancy_threshold_8, launch_threshold_pos_8,
          occupancy_threshold_pos_8, launch_split_8, occupancy_split_8},
-        {10, launch_threshold_10, occupancy_threshold_10, launch_threshold_pos_10,
+        {10, launch_staged_10, occupancy_staged_10, launch_threshold_10,
+         occupancy_threshold_10, launch_threshold_pos_10,
          occupancy_threshold_pos_10, nullptr, nullptr},
-        {12, launch_threshold_12, occupancy_threshold_12, launch_threshold_pos_12,
+        {12, launch_staged_12, occupancy_staged_12, launch_threshold_12,
+         occupancy_threshold_12, launch_threshold_pos_12,
          occupancy_threshold_pos_12, nullptr, nullptr},
-        {16, launch_threshold_16, occupancy_threshold_16, launch_threshold_pos_16,
+        {16, launch_staged_16, occupancy_staged_16, launch_threshold_16,
+         occupancy_threshold_16, launch_threshold_pos_16,
          occupancy_threshold_pos_16, nullptr, nullptr},
     };
     *count = int(sizeof tab / sizeof tab[0]);
@@ -361,16 +372,20 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         if (d_mpos) cudaFree(d_mpos);
         if (d_ttab) cudaFree(d_ttab);
     };
-    if ((e = cudaMalloc(&idx->d_words, sizeof(uint64_t) * std::max<uint64_t>(total, 1))) != cudaSuccess ||
+    // two zero words after the streams: the staged kernel copies whole 16-byte
+    // units, which may run one word past a stream's last word
+    if ((e = cudaMalloc(&idx->d_words, sizeof(uint64_t) * (total + 2))) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_mtab, sizeof(uint2) * moff)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_sdesc, sizeof(uint64_t) * sdesc_n)) != cudaSuccess ||
+        (e = cudaMalloc(&idx->d_sseg, sizeof(uint64_t) * sdesc_n)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_desc, sizeof(BitmapDesc) * nbitmaps)) != cudaSuccess ||
         (e = cudaMalloc(&d_ttab, sizeof(uint32_t) * ttab_n)) != cudaSuccess ||
         (e = cudaMalloc(&d_mpos, sizeof(uint32_t) * std::max<uint64_t>(mpos.size(), 1))) != cudaSuccess) {
         free_tmp();
         return cleanup(cuda_fail(e, "index allocation"));
     }
-    if ((e = cudaMemcpyAsync(idx->d_words, words, sizeof(uint64_t) * total,
+    if ((e = cudaMemsetAsync(idx->d_words + total, 0, 2 * sizeof(uint64_t), st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(idx->d_words, words, sizeof(uint64_t) * total,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_mpos, mpos.data(), sizeof(uint32_t) * mpos.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -392,7 +407,8 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         return cleanup(cuda_fail(e, "index allocation"));
     }
     e = launch_index_build_a(idx->d_words, d_mpos, idx->d_desc, idx->d_mtab, d_ttab,
-                             idx->d_sdesc, d_mcount, nbitmaps, idx->W, idx->NG, st);
+                             idx->d_sdesc, idx->d_sseg, d_mcount, nbitmaps, idx->W, idx->NG,
+                             st);
     std::vector<uint32_t> mcount(nbitmaps);
     std::vector<uint64_t> mbase(nbitmaps);
     if (e == cudaSuccess)
@@ -413,7 +429,7 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = launch_index_build_b(idx->d_mtab, d_ttab, idx->d_desc, d_mbase, idx->d_sdesc,
-                                 idx->d_masks, nbitmaps, idx->W, idx->NG, st);
+                                 idx->d_sseg, idx->d_masks, nbitmaps, idx->W, idx->NG, st);
     if (e == cudaSuccess)
         e = cudaMalloc(&idx->d_pcls, sizeof(uint64_t) * uint64_t(nbitmaps) * ((idx->NG + 31) / 32));
     if (e == cudaSuccess) e = launch_pack_classes(idx->d_sdesc, idx->d_pcls, nbitmaps, idx->NG, st);
@@ -435,6 +451,7 @@ void idx_free(thr_index* idx) {
     cudaFree(idx->d_sdesc);
     cudaFree(idx->d_pcls);
     cudaFree(idx->d_masks);
+    cudaFree(idx->d_sseg);
     cudaFree(idx->d_desc);
     cudaSetDevice(cur);
     delete idx;

@@ -16,6 +16,12 @@
 //          ceil(NG / 32) words per bitmap: classification reads these and
 //          the full descriptor only for inputs with literals.
 //   masks  one 64-byte MaskRec per mixed (bitmap, subtile).
+//   sseg   per bitmap and subtile one uint64 segment descriptor: the stream
+//          index (relative to the bitmap's first word) of the first word the
+//          subtile's literals need, | their number of stream words << 32
+//          (a literal run: its literals; mixed: the literals and the markers
+//          between them, from MaskRec::base on; else 0).  The staged kernel
+//          copies exactly these words to shared memory.
 //
 // A query (or a batch of them) runs in three passes:
 //   A  k_threshold<S> / k_scancount: persistent grid; a warp takes a work
@@ -112,6 +118,10 @@ struct PassAParams {
     const uint64_t* sdesc;  // subtile descriptors, NG per bitmap
     const uint64_t* pcls;   // packed subtile classes, NGW words per bitmap
     const MaskRec* masks;   // mask records of the mixed subtiles
+    const uint64_t* sseg;   // segment descriptors, NG per bitmap
+    uint32_t* err;          // set to a non-zero code when a kernel gave up waiting
+    uint32_t lose;          // test hook: each staged slot expects 16 bytes more than
+                            // it is sent, so its wait runs out (THR_TEST_LOST_COPY)
     const BitmapDesc* desc;
     const QDesc* qd;        // the chunk's queries, by slot
     const uint32_t* ids;    // every id of the batch
@@ -344,7 +354,7 @@ __device__ __forceinline__ RangeAgg agg_load_plain(const uint32_t* p) {
 // host has placed the mask records: the mask records and final descriptors.
 cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
                                  const BitmapDesc* desc, uint2* mtab, uint32_t* ttab,
-                                 uint64_t* sdesc, uint32_t* mixed_count,
+                                 uint64_t* sdesc, uint64_t* sseg, uint32_t* mixed_count,
                                  uint32_t nbitmaps, uint32_t W, uint32_t NG,
                                  cudaStream_t st);
 // Packed classes from the final subtile descriptors (after part b).
@@ -352,7 +362,7 @@ cudaError_t launch_pack_classes(const uint64_t* sdesc, uint64_t* pcls, uint32_t 
                                 uint32_t NG, cudaStream_t st);
 cudaError_t launch_index_build_b(const uint2* mtab, const uint32_t* ttab,
                                  const BitmapDesc* desc, const uint64_t* mixed_base,
-                                 uint64_t* sdesc, MaskRec* masks, uint32_t nbitmaps,
-                                 uint32_t W, uint32_t NG, cudaStream_t st);
+                                 uint64_t* sdesc, uint64_t* sseg, MaskRec* masks,
+                                 uint32_t nbitmaps, uint32_t W, uint32_t NG, cudaStream_t st);
 
 }  // namespace thr

@@ -2,6 +2,7 @@
 #include "thr_exec.h"
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "thr_launch.h"
 
@@ -41,6 +42,7 @@ cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t s
         case 2: return tab[w].launch_pos(p, grid, st);
         case 3: return tab[w].launch_split ? tab[w].launch_split(p, grid, st)
                                            : cudaErrorInvalidValue;
+        case 5: return tab[w].launch_direct(p, grid, st);
         default: return tab[w].launch(p, grid, st);
     }
 }
@@ -48,6 +50,11 @@ cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t s
 }  // namespace
 
 uint32_t scan_blocks(uint32_t NG) { return (NG + 255) / 256; }
+
+uint32_t test_lost_copy() {
+    const char* v = std::getenv("THR_TEST_LOST_COPY");
+    return (v && v[0] == '1') ? 1u : 0u;
+}
 
 uint64_t scratch_per_slot(uint32_t W, uint32_t NG) {
     const uint64_t NB = scan_blocks(NG);
@@ -61,6 +68,7 @@ ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
     ScratchLayout l{};
     l.gtick = 0;
     l.base = 8;
+    l.err = 16;  // a kernel that gave up waiting writes its code here
     l.work = 256;
     l.tick = l.work + r256(4 * nlaunch);
     l.res = l.tick + r256(4 * Q);
@@ -106,6 +114,10 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
         return;
     }
     choose_class(n, T, cls, zmode);
+    if (v == kVarDirect) {
+        *cls += kClassDirect;
+        return;
+    }
     if (v == kVarSplit) {
         if (*cls < kSplitWidths) *cls += kClassSplit;
         return;
@@ -138,6 +150,7 @@ cudaError_t class_occupancy(int cls, int* per_sm) {
         case 2: return tab[w].occupancy_pos(per_sm);
         case 3: return tab[w].occupancy_split ? tab[w].occupancy_split(per_sm)
                                               : cudaErrorInvalidValue;
+        case 5: return tab[w].occupancy_direct(per_sm);
         default: return tab[w].occupancy(per_sm);
     }
 }
@@ -159,6 +172,9 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     p.pcls = idx->d_pcls;
     p.NGW = (NG + 31) / 32;
     p.masks = idx->d_masks;
+    p.sseg = idx->d_sseg;
+    p.err = reinterpret_cast<uint32_t*>(s + l.err);
+    p.lose = test_lost_copy();
     p.desc = idx->d_desc;
     p.ids = b.ids;
     p.W = idx->W;

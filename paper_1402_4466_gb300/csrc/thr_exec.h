@@ -14,11 +14,13 @@
 namespace thr {
 
 // Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
-// kernel_table()[c].S (grouped decode), kClassScanCount the ScanCount
-// kernel, kClassPos + c carry-save of width kernel_table()[c].S with the
-// position-major decode of mixed inputs, kClassSplit + c carry-save with
-// the inputs split among the CTA's warps (widths up to kSplitWidths),
-// kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax).
+// kernel_table()[c].S (staged inputs, grouped decode), kClassScanCount the
+// ScanCount kernel, kClassPos + c carry-save of width kernel_table()[c].S
+// with the position-major decode of mixed inputs, kClassSplit + c carry-save
+// with the inputs split among the CTA's warps (widths up to kSplitWidths),
+// kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax),
+// kClassDirect + c carry-save of width kernel_table()[c].S loading every
+// word from global memory (the grouped decode without staging).
 constexpr int kNumWidths = 11;
 constexpr int kSplitWidths = 8;  // S = 1..8
 constexpr int kLoopedMax = 4;    // Looped levels (thresholds) instantiated
@@ -26,21 +28,29 @@ constexpr int kClassScanCount = kNumWidths;
 constexpr int kClassPos = kNumWidths + 1;
 constexpr int kClassSplit = 2 * kNumWidths + 1;
 constexpr int kClassLooped = kClassSplit + kSplitWidths;
-constexpr int kNumClasses = kClassLooped + kLoopedMax;
+constexpr int kClassDirect = kClassLooped + kLoopedMax;
+constexpr int kNumClasses = kClassDirect + kNumWidths;
 static_assert(kNumClasses <= 64, "class sets are 64-bit masks");
-// Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major,
-// 3 split inputs, 4 Looped.
-constexpr int kNumFamilies = 5;
+// Family of a class: 0 staged carry-save, 1 ScanCount, 2 position-major,
+// 3 split inputs, 4 Looped, 5 direct carry-save.
+constexpr int kNumFamilies = 6;
 inline int class_family(int c) {
-    return c < kNumWidths ? 0
-                          : (c == kClassScanCount ? 1
-                                                  : (c < kClassSplit ? 2 : (c < kClassLooped ? 3 : 4)));
+    return c < kNumWidths
+               ? 0
+               : (c == kClassScanCount
+                      ? 1
+                      : (c < kClassSplit ? 2
+                                         : (c < kClassLooped ? 3 : (c < kClassDirect ? 4 : 5))));
 }
 // Counter-width index of a carry-save class (levels - 1 for Looped).
 inline int class_width(int c) {
-    return c < kNumWidths ? c
-                          : (c < kClassSplit ? c - kClassPos
-                                             : (c < kClassLooped ? c - kClassSplit : c - kClassLooped));
+    return c < kNumWidths
+               ? c
+               : (c < kClassSplit
+                      ? c - kClassPos
+                      : (c < kClassLooped ? c - kClassSplit
+                                          : (c < kClassDirect ? c - kClassLooped
+                                                              : c - kClassDirect)));
 }
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
@@ -64,7 +74,7 @@ struct ChunkPlan {
 // Byte offsets of the scratch regions for chunks of at most Q slots and
 // nlaunch pass-A launches in all.
 struct ScratchLayout {
-    size_t gtick, base, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
+    size_t gtick, base, err, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
 };
 ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
                              uint64_t nlaunch);
@@ -112,7 +122,10 @@ constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2, kVarSplit = 3;
 constexpr int kNumVariants = 4;  // the policies' choices
 //   kVarLooped     Looped levels (Sec. 6.2) for 1 <= T <= kLoopedMax, T <= n
 //                  (else kVarCsa runs); chosen by flag only
+//   kVarDirect     kVarCsa without staging: every word loaded from global
+//                  memory where it is added; chosen by flag only
 constexpr int kVarLooped = 4;
+constexpr int kVarDirect = 5;
 // Kernel class and zero counting of a query run with variant v.
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 
@@ -122,6 +135,11 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 // class is the first instantiated width that fits.
 int slices_for(uint64_t t);  // the fewest S >= 1 with 2^S >= t
 void choose_class(uint32_t n, uint32_t T, int* cls, uint32_t* zmode);
+
+// THR_TEST_LOST_COPY=1 in the environment (tests only): every staged slot
+// waits for 16 bytes that are never sent, so the kernel's bounded wait runs
+// out and the call returns THR_E_TIMEOUT.
+uint32_t test_lost_copy();
 
 // CTAs per SM of a class's kernel at full occupancy.
 cudaError_t class_occupancy(int cls, int* per_sm);

@@ -22,11 +22,12 @@ struct thr_index {
     uint32_t NG = 0;  // ceil(W / 128)
     uint64_t total_words = 0;
     uint64_t total_markers = 0;
-    uint64_t* d_words = nullptr;
+    uint64_t* d_words = nullptr;  // total_words + 2 (zero pad: 16-byte copies may round up)
     uint2* d_mtab = nullptr;
     uint64_t* d_sdesc = nullptr;  // NG subtile descriptors per bitmap
     uint64_t* d_pcls = nullptr;   // their classes, 2 bits each, ceil(NG/32) words per bitmap
     thr::MaskRec* d_masks = nullptr;  // mask records of the mixed subtiles
+    uint64_t* d_sseg = nullptr;   // NG segment descriptors per bitmap
     uint64_t mixed_subtiles = 0;
     thr::BitmapDesc* d_desc = nullptr;
     std::vector<thr::BitmapDesc> desc;

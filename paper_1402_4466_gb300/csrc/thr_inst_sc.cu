@@ -1,0 +1,8 @@
+// Staged query kernel instantiations for counter widths 10, 12 and 16.
+#include "thr_inst_macro.cuh"
+
+namespace thr {
+THR_DEFINE_STAGED(10)
+THR_DEFINE_STAGED(12)
+THR_DEFINE_STAGED(16)
+}  // namespace thr

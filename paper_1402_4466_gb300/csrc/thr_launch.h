@@ -13,8 +13,10 @@ using OccupancyFn = cudaError_t (*)(int* blocks_per_sm);
 
 struct KernelEntry {
     int S;
-    LaunchFn launch;          // grouped decode
+    LaunchFn launch;          // staged inputs (thr_staged.cuh), grouped decode
     OccupancyFn occupancy;
+    LaunchFn launch_direct;   // grouped decode loading every word from global memory
+    OccupancyFn occupancy_direct;
     LaunchFn launch_pos;      // position-major decode of mixed inputs
     OccupancyFn occupancy_pos;
     LaunchFn launch_split;    // inputs split among the CTA's warps (S <= 8), or null
@@ -38,6 +40,22 @@ const KernelEntry* kernel_table(int* count);
     cudaError_t occupancy_threshold_##S(int*);                                   \
     cudaError_t launch_threshold_pos_##S(const PassAParams&, int, cudaStream_t); \
     cudaError_t occupancy_threshold_pos_##S(int*);
+
+#define THR_DECLARE_STAGED(S)                                              \
+    cudaError_t launch_staged_##S(const PassAParams&, int, cudaStream_t);     \
+    cudaError_t occupancy_staged_##S(int*);
+
+THR_DECLARE_STAGED(1)
+THR_DECLARE_STAGED(2)
+THR_DECLARE_STAGED(3)
+THR_DECLARE_STAGED(4)
+THR_DECLARE_STAGED(5)
+THR_DECLARE_STAGED(6)
+THR_DECLARE_STAGED(7)
+THR_DECLARE_STAGED(8)
+THR_DECLARE_STAGED(10)
+THR_DECLARE_STAGED(12)
+THR_DECLARE_STAGED(16)
 
 #define THR_DECLARE_SPLIT(S)                                                \
     cudaError_t launch_split_##S(const PassAParams&, int, cudaStream_t);     \

@@ -144,10 +144,16 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
         cudaSuccess)
         return cuda_error(e, "launch query kernels");
     unsigned long long h[2] = {0, 0};
+    uint32_t kerr = 0;
     if ((e = cudaMemcpyAsync(h, b.scratch + lay.res, sizeof h, cudaMemcpyDeviceToHost, st)) !=
-        cudaSuccess)
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(&kerr, b.scratch + lay.err, sizeof kerr, cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
         return cuda_error(e, "read result length");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "query");
+    if (kerr)
+        return report_error(THR_E_TIMEOUT,
+                            "a query kernel gave up waiting for its shared-memory copies");
     *out_len = h[1];
     if (*out_len > cap) return report_error(THR_E_NOSPACE, "output buffer too small");
     return THR_OK;

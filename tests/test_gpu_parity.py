@@ -306,6 +306,57 @@ def test_split_many_criteria_full_size(many_criteria_full):
         p.check(list(range(synth.MANY_N)), T, SPLIT)
 
 
+# ---- the default kernel's staged copies: stream segments that start at odd
+#      and even stream words, sparse inputs packed several to a ring slot,
+#      and the last words of the index
+
+def test_staged_segments_alignment_and_index_end():
+    r = (1 << 16) * 64 + 5  # W even + 1: the streams' parities alternate
+    rng = np.random.default_rng(707)
+    arrays = []
+    for k in range(12):
+        if k % 3 == 0:  # every word a literal: literal-run subtiles
+            w = rng.integers(1, 1 << 62, size=synth.nwords(r), dtype=np.int64).astype(np.uint64)
+            w[-1] &= np.uint64((1 << (r % 64)) - 1)
+            w[-1] |= np.uint64(1)
+            arrays.append(w)
+        elif k % 3 == 1:
+            arrays.append(synth.bernoulli(707, k, r, 3e-4))
+        else:
+            arrays.append(synth.clustered(707, k, r, 0.02))
+    # the last bitmap: dense to its very last word (the end of the index)
+    w = rng.integers(1, 1 << 62, size=synth.nwords(r), dtype=np.int64).astype(np.uint64)
+    w[-1] = np.uint64((1 << (r % 64)) - 1) & np.uint64(0b10101)
+    arrays.append(w)
+    p = Pair(arrays, r)
+    n = len(arrays)
+    for T in (1, 2, 3, 4, 5, 7, n):
+        p.check(list(range(n)), T)
+        p.check(list(range(n))[::-1] + [n - 1, 0], T)
+
+
+# ---- the grouped carry-save decode loading every word from global memory
+
+DIRECT = thr.THR_VARIANT_DIRECT
+
+
+def test_direct_random_tiny_all_thresholds():
+    rng = np.random.default_rng(505)
+    for _ in range(20):
+        n = int(rng.integers(1, 13))
+        r = int(rng.choice([1, 63, 64, 65, 1000, 4096, 9000, 40000]))
+        p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
+        for T in range(0, n + 2):
+            p.check(list(range(n)), T, DIRECT)
+
+
+def test_direct_many_criteria_full_size(many_criteria_full):
+    words, r = many_criteria_full
+    p = Pair(words, r)
+    for T in (*synth.MANY_TS, 1, 64):
+        p.check(list(range(synth.MANY_N)), T, DIRECT)
+
+
 # ---- the Looped levels (Algorithm 3, Sec. 6.2) for T <= 4
 
 LOOPED = thr.THR_VARIANT_LOOPED
@@ -384,3 +435,24 @@ def test_symmetric_many_criteria_full_size(many_criteria_full):
     for lo, hi in ((0, 1), (1, 1), (2, 4), (5, 64)):
         _check_sym(p, ids, lo, hi)
     _check_sym(p, ids, 0, 0, odd=True)
+
+
+# ---- a staged copy that never arrives: the bounded wait gives up
+
+def test_lost_copy_returns_timeout_and_context_survives(monkeypatch):
+    """Host-side fault injection: with THR_TEST_LOST_COPY=1 every ring slot
+    waits for 16 bytes that are never sent.  The warp's wait gives up after
+    about a second, the call returns THR_E_TIMEOUT, and the same query then
+    runs exactly (the context is still usable)."""
+    r = 640
+    rng = np.random.default_rng(808)
+    p = from_ints(oracle_pins.random_bitsets(rng, 3, r), r)
+    monkeypatch.setenv("THR_TEST_LOST_COPY", "1")
+    dense = [oracle_pins.mask(r) & int(x) for x in (0x5555 << 8, 0xF0F0F0F0F0F0F0F0F0F0)]
+    q = from_ints(dense + [oracle_pins.mask(r) & 0x123456789ABCDEF], r)
+    with pytest.raises(thr.ThrError) as e:
+        thr.thr_query(q.g, [0, 1, 2], 2)
+    assert e.value.status == thr.THR_E_TIMEOUT
+    monkeypatch.delenv("THR_TEST_LOST_COPY")
+    q.check([0, 1, 2], 2)
+    p.check([0, 1, 2], 2)
