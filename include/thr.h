@@ -31,7 +31,9 @@
  *                 words.  Inputs must be canonical; outputs always are.
  *
  * Limits: 1 <= r and W = ceil(r/64) <= 2^31 - 2 (so no counter overflows and
- * word indices fit 31 bits); 1 <= n <= 65536 bitmaps per query.
+ * word indices fit 31 bits); 1 <= n <= THR_MAX_IDS = 2^20 - 1 bitmap ids per
+ * query (a million inputs: the per-row counts then need at most 20 bits);
+ * opt-threshold queries take at most 65535.
  *
  * Errors: every call returns a thr_status; no C++ exception crosses the ABI.
  * thr_last_error() describes the last failure of the calling thread.
@@ -51,6 +53,8 @@ extern "C" {
 #endif
 
 typedef struct thr_index thr_index; /* opaque; owns all device memory */
+
+#define THR_MAX_IDS 1048575u /* bitmap ids (with repeats) per query: 2^20 - 1 */
 
 typedef enum {
     THR_OK = 0,
@@ -137,7 +141,7 @@ thr_status idx_build_rle(const uint64_t *words, const uint64_t *offsets,
  *   idx       index from idx_build_rle
  *   ids       host array of n bitmap ids (< nbitmaps; duplicates count with
  *             multiplicity)
- *   n         1 <= n <= 65536
+ *   n         1 <= n <= THR_MAX_IDS
  *   T         any value; 0 gives every row, > n gives none
  *   out       caller-owned buffer of cap words: host memory, or device memory
  *             of the index's GPU (or managed memory) when flags has
@@ -195,6 +199,24 @@ thr_status thr_query_sym(const thr_index *idx, const uint32_t *ids, uint32_t n, 
 thr_status thr_query_opt(const thr_index *idx, const uint32_t *ids, uint32_t n, uint64_t K,
                          uint32_t *T_out, uint64_t *out, uint64_t cap, uint64_t *out_len,
                          uint32_t flags, void *cuda_stream);
+
+/*
+ * The profiling pass of thr_query_opt alone, for callers that combine
+ * partial answers, such as the row shards of an index split by rows (Sec. 9
+ * asks about partitioning the problem): *T_out receives this index's answer
+ * T* for K (as thr_query_opt; 0 when no T qualifies) and hist[c], c = 0..n,
+ * the number of rows whose count over ids is exactly c, exact for every
+ * c >= max(*T_out, 1); bins below may be incomplete and hist[0] is 0 (not
+ * computed).  Over shards g with answers T_g, the answer of the whole is at
+ * least max_g T_g, and every shard's bins are exact from there up, so the
+ * whole's answer is the first c from n down to max(max_g T_g, 1) whose
+ * summed suffix hist[c] + .. + hist[n] reaches K (0 if none does).
+ *   n      1..65535;  K >= 1;  hist: host array of n + 1 words
+ * Synchronous on cuda_stream; errors as thr_query.
+ */
+thr_status thr_query_opt_hist(const thr_index *idx, const uint32_t *ids, uint32_t n,
+                              uint64_t K, uint32_t *T_out, uint64_t *hist,
+                              void *cuda_stream);
 
 /*
  * nq opt-threshold queries (as thr_query_opt) in one profiling launch per

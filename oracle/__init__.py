@@ -101,9 +101,11 @@ class Oracle:
         lib.orc_threshold_parts.argtypes = [u64p, u64p, u32, u64, u32p, u32, u32, u32,
                                             u64p, u64, u64p]
         lib.orc_max_threads.argtypes = []
+        lib.orc_count_histogram.argtypes = [u64p, u64p, u32, u64, u32p, u32, u64p]
         for f in (lib.orc_encode, lib.orc_decode, lib.orc_validate,
                   lib.orc_threshold, lib.orc_threshold_words, lib.orc_symmetric,
-                  lib.orc_opt_threshold, lib.orc_threshold_parts, lib.orc_max_threads):
+                  lib.orc_opt_threshold, lib.orc_threshold_parts, lib.orc_max_threads,
+                  lib.orc_count_histogram):
             f.restype = ctypes.c_int
         self.c = lib
 
@@ -150,6 +152,18 @@ class Oracle:
         if rc != OK:
             raise OracleError(rc, "threshold")
         return out[: n.value].copy()
+
+    def count_histogram(self, words, offsets, r: int, ids) -> np.ndarray:
+        """hist[c], c = 0..n: the rows counted exactly c times over ids."""
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        hist = np.zeros(ids.size + 1, dtype=np.uint64)
+        rc = self.c.orc_count_histogram(_p64(words), _p64(offsets), len(offsets) - 1, int(r),
+                                        _p32(ids), ids.size, _p64(hist))
+        if rc != OK:
+            raise OracleError(rc, "count_histogram")
+        return hist
 
     def max_threads(self) -> int:
         """Threads the row-partitioned query may use (1 without OpenMP)."""
@@ -274,6 +288,9 @@ class Index:
     def threshold_words(self, ids, T: int) -> np.ndarray:
         return self._o().threshold_words(self.words, self.offsets, self.r,
                                          ids, T)
+
+    def count_histogram(self, ids) -> np.ndarray:
+        return self._o().count_histogram(self.words, self.offsets, self.r, ids)
 
     def threshold_parts(self, ids, T: int, parts: int) -> np.ndarray:
         return self._o().threshold_parts(self.words, self.offsets, self.r, ids, T, parts)

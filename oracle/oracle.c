@@ -472,3 +472,41 @@ int orc_threshold_parts(const uint64_t *streams, const uint64_t *offsets,
     free(words);
     return rc;
 }
+
+/*
+ * The histogram of the counts (Sec. 5.1: ScanCount's counters, then the
+ * opt-threshold reasoning of Sec. 3.3 reads them by count): hist[c], c = 0..n,
+ * receives the number of rows in [0, r) counted exactly c times over the
+ * multiset ids.  The suffix sum hist[T] + .. + hist[n] is the size of the
+ * T-overlap result; row shards can add their histograms bin by bin.
+ */
+int orc_count_histogram(const uint64_t *streams, const uint64_t *offsets,
+                        uint32_t nbitmaps, uint64_t r, const uint32_t *ids,
+                        uint32_t n, uint64_t *hist)
+{
+    uint32_t *count = NULL;
+    uint64_t *rows = NULL;
+    int rc = ORC_OK;
+    if ((n > 0 && ids == NULL) || offsets == NULL || hist == NULL) return ORC_E_INVAL;
+    for (uint32_t q = 0; q < n; q++)
+        if (ids[q] >= nbitmaps) return ORC_E_INVAL;
+    count = (uint32_t *)calloc(r > 0 ? r : 1, sizeof(uint32_t));
+    rows = (uint64_t *)malloc((r > 0 ? r : 1) * sizeof(uint64_t));
+    if (!count || !rows) {
+        rc = ORC_E_NOMEM;
+        goto done;
+    }
+    for (uint32_t q = 0; q < n; q++) {
+        uint64_t b = ids[q], nr = 0;
+        rc = orc_decode(streams + offsets[b], offsets[b + 1] - offsets[b], r,
+                        rows, r, &nr);
+        if (rc != ORC_OK) goto done;
+        for (uint64_t k = 0; k < nr; k++) count[rows[k]]++;
+    }
+    for (uint32_t c = 0; c <= n; c++) hist[c] = 0;
+    for (uint64_t x = 0; x < r; x++) hist[count[x]]++;
+done:
+    free(count);
+    free(rows);
+    return rc;
+}

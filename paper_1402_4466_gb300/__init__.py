@@ -33,6 +33,7 @@ THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x4
 THR_VARIANT_SPLIT = 0x600
 THR_VARIANT_LOOPED = 0x800
 THR_VARIANT_DIRECT = 0xA00
+THR_MAX_IDS = 1048575  # bitmap ids (with repeats) per query: 2^20 - 1
 THR_VARIANT_MASK = 0xE00
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
@@ -48,7 +49,7 @@ ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_stati
                "thr_index_set_selector", "thr_server_create", "thr_server_submit",
                "thr_server_wait", "thr_server_stats", "thr_server_free", "thr_rle_encode_rows",
                "thr_rle_slice", "thr_rle_stitch", "thr_query_sym", "thr_query_opt",
-               "thr_query_opt_batch",
+               "thr_query_opt_batch", "thr_query_opt_hist",
                "idx_info", "thr_rle_encode", "thr_rle_validate",
                "thr_last_kernel_ms", "thr_last_error")
 
@@ -91,6 +92,7 @@ def load():
             lib.thr_query_opt.argtypes = [vp, vp, u32, u64, u32p, vp, u64, u64p, u32, vp]
             lib.thr_query_opt_batch.argtypes = [vp, u32, vp, vp, vp, vp, vp, u64, vp, vp, u32,
                                                 vp]
+            lib.thr_query_opt_hist.argtypes = [vp, vp, u32, u64, u32p, vp, vp]
             lib.thr_rle_stitch.argtypes = [vp, vp, vp, u32, vp, u64, u64p]
             lib.thr_last_error.argtypes = []
             lib.thr_last_error.restype = ctypes.c_char_p
@@ -128,7 +130,7 @@ def load():
                       "thr_selector_gradients", "thr_query_features", "thr_index_set_selector",
                       "thr_server_create", "thr_server_submit", "thr_server_wait",
                       "thr_server_stats", "thr_rle_encode_rows", "thr_rle_slice",
-                      "thr_rle_stitch", "thr_query_sym"):
+                      "thr_rle_stitch", "thr_query_sym", "thr_query_opt_hist"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -294,6 +296,20 @@ def thr_query_opt(idx: Index, ids, K: int = 1, out=None, stream=None, flags: int
                              int(size), ctypes.byref(n), flags,
                              ctypes.c_void_p(_stream(stream))), "thr_query_opt")
     return T.value, n.value
+
+
+def thr_query_opt_hist(idx: Index, ids, K: int = 1, stream=None):
+    """The profiling pass of an opt-threshold query alone: (T, hist) with T
+    this index's answer for K and hist[c] (c = 0..n) the rows counted exactly
+    c times, exact for every c >= max(T, 1) (hist[0] is not computed)."""
+    ids = _u32(ids)
+    hist = np.zeros(ids.size + 1, dtype=np.uint64)
+    T = ctypes.c_uint32(0)
+    _check(load().thr_query_opt_hist(ctypes.c_void_p(idx.handle),
+                                     ctypes.c_void_p(ids.ctypes.data), ids.size, int(K),
+                                     ctypes.byref(T), ctypes.c_void_p(hist.ctypes.data),
+                                     ctypes.c_void_p(_stream(stream))), "thr_query_opt_hist")
+    return int(T.value), hist
 
 
 def thr_query_opt_batch(idx: Index, queries, pool=None, flags: int = 0, stream=None):

@@ -163,6 +163,9 @@ const KernelEntry* kernel_table(int* count) {
         {16, launch_staged_16, occupancy_staged_16, launch_threshold_16,
          occupancy_threshold_16, launch_threshold_pos_16,
          occupancy_threshold_pos_16, nullptr, nullptr},
+        {20, launch_staged_20, occupancy_staged_20, launch_threshold_20,
+         occupancy_threshold_20, launch_threshold_pos_20,
+         occupancy_threshold_pos_20, nullptr, nullptr},
     };
     *count = int(sizeof tab / sizeof tab[0]);
     return tab;
@@ -185,8 +188,8 @@ static thr_status check_batch(const thr_index* idx, uint32_t nq, const uint32_t*
     for (uint32_t q = 0; q < nq; ++q) {
         if (id_off[q + 1] < id_off[q]) return fail(THR_E_INVAL, "id_off decreases at %u", q);
         const uint32_t n = id_off[q + 1] - id_off[q];
-        if (n == 0 || n > 65536)
-            return fail(THR_E_INVAL, "query %u: n must be in 1..65536", q);
+        if (n == 0 || n > THR_MAX_IDS)
+            return fail(THR_E_INVAL, "query %u: n must be in 1..%u", q, THR_MAX_IDS);
     }
     for (uint64_t i = 0; i < id_off[nq]; ++i)
         if (ids[i] >= idx->nbitmaps)
@@ -471,7 +474,7 @@ thr_status thr_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
                      uint32_t flags, void* cuda_stream) {
     if (!idx || !ids || !out_len || (cap > 0 && !out))
         return fail(THR_E_INVAL, "null argument");
-    if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
+    if (n == 0 || n > THR_MAX_IDS) return fail(THR_E_INVAL, "n must be in 1..%u", THR_MAX_IDS);
     if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK))
         return fail(THR_E_INVAL, "unknown flags");
     const bool profile = flags & THR_PROFILE;
@@ -559,7 +562,7 @@ thr_status thr_query_sym(const thr_index* idx, const uint32_t* ids, uint32_t n, 
                          uint32_t hi, uint64_t* out, uint64_t cap, uint64_t* out_len,
                          uint32_t flags, void* cuda_stream) {
     if (!idx || !ids || !out_len || (cap > 0 && !out)) return fail(THR_E_INVAL, "null argument");
-    if (n == 0 || n > 65536) return fail(THR_E_INVAL, "n must be in 1..65536");
+    if (n == 0 || n > THR_MAX_IDS) return fail(THR_E_INVAL, "n must be in 1..%u", THR_MAX_IDS);
     if (flags & ~(THR_OUT_DEVICE | THR_SYM_ODD | THR_PROFILE))
         return fail(THR_E_INVAL, "unknown flags");
     for (uint32_t i = 0; i < n; ++i)
@@ -656,6 +659,25 @@ thr_status thr_query_opt(const thr_index* idx, const uint32_t* ids, uint32_t n, 
     s = thr_query(idx, ids, n, *T_out, out, cap, out_len, flags & ~THR_PROFILE, cuda_stream);
     if (flags & THR_PROFILE) g_kernel_ms = ms;
     return s;
+}
+
+thr_status thr_query_opt_hist(const thr_index* idx, const uint32_t* ids, uint32_t n,
+                              uint64_t K, uint32_t* T_out, uint64_t* hist,
+                              void* cuda_stream) {
+    if (!idx || !ids || !T_out || !hist) return fail(THR_E_INVAL, "null argument");
+    if (n == 0 || n > 65535) return fail(THR_E_INVAL, "n must be in 1..65535");
+    if (K == 0) return fail(THR_E_INVAL, "K must be >= 1");
+    for (uint32_t i = 0; i < n; ++i)
+        if (ids[i] >= idx->nbitmaps)
+            return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
+    const uint32_t id_off[2] = {0, n};
+    std::vector<unsigned long long> h;
+    thr_status s = opt_profile(idx, 1, id_off, ids, &K, T_out, (cudaStream_t)cuda_stream,
+                               nullptr, &h);
+    if (s != THR_OK) return s;
+    for (uint32_t c = 0; c <= n; ++c) hist[c] = h[c];
+    hist[0] = 0;  // not counted by the profiling pass
+    return THR_OK;
 }
 
 thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id_off,

@@ -51,7 +51,7 @@ constexpr int kNT = 32 * kNW;     // threads per CTA
 constexpr int kTW = kGW * kNW;    // words per CTA tile
 constexpr int kWPL = 4;           // consecutive words per lane
 constexpr int kCH = 128;          // input records per warp and chunk
-constexpr int kSMax = 16;         // largest counter width instantiated
+constexpr int kSMax = 20;         // largest counter width instantiated
 
 // Mask record of a mixed (bitmap, subtile), one 64-byte line.  Bit j of
 // word w of lm / cm / om is subtile word x0 + 32 w + j being a literal /

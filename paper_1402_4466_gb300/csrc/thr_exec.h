@@ -21,7 +21,7 @@ namespace thr {
 // kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax),
 // kClassDirect + c carry-save of width kernel_table()[c].S loading every
 // word from global memory (the grouped decode without staging).
-constexpr int kNumWidths = 11;
+constexpr int kNumWidths = 12;
 constexpr int kSplitWidths = 8;  // S = 1..8
 constexpr int kLoopedMax = 4;    // Looped levels (thresholds) instantiated
 constexpr int kClassScanCount = kNumWidths;

@@ -56,6 +56,7 @@ THR_DECLARE_STAGED(8)
 THR_DECLARE_STAGED(10)
 THR_DECLARE_STAGED(12)
 THR_DECLARE_STAGED(16)
+THR_DECLARE_STAGED(20)
 
 #define THR_DECLARE_SPLIT(S)                                                \
     cudaError_t launch_split_##S(const PassAParams&, int, cudaStream_t);     \
@@ -81,5 +82,6 @@ THR_DECLARE_WIDTH(8)
 THR_DECLARE_WIDTH(10)
 THR_DECLARE_WIDTH(12)
 THR_DECLARE_WIDTH(16)
+THR_DECLARE_WIDTH(20)
 
 }  // namespace thr

@@ -55,7 +55,8 @@ constexpr uint32_t kNarrowCounts = 15;
 // and ovf[q] (host) tells which queries must run again.
 thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                         const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
-                        float* ms, bool exact, std::vector<uint32_t>* ovf_out) {
+                        float* ms, bool exact, std::vector<uint32_t>* ovf_out,
+                        std::vector<unsigned long long>* hist_out) {
     int nt = 0;
     const OptEntry* tab = opt_kernel_table(&nt);
     const uint64_t nids = id_off[nq];
@@ -173,6 +174,7 @@ thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_of
     }
     OPT_CK(cudaStreamSynchronize(st), "opt profiling");
     if (ms) OPT_CK(cudaEventElapsedTime(ms, ev[0], ev[1]), "profiling time");
+    if (hist_out) *hist_out = hist;
     // the first count from the top whose suffix holds K rows
     for (uint32_t q = 0; q < nq; ++q) {
         const uint32_t n = id_off[q + 1] - id_off[q];
@@ -192,11 +194,11 @@ thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_of
 
 thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                        const uint32_t* ids, const uint64_t* K, uint32_t* T, cudaStream_t st,
-                       float* ms) {
+                       float* ms, std::vector<unsigned long long>* hist) {
     std::vector<uint32_t> ovf;
     float ms1 = 0.f;
     thr_status s =
-        profile_pass(idx, nq, id_off, ids, K, T, st, ms ? &ms1 : nullptr, false, &ovf);
+        profile_pass(idx, nq, id_off, ids, K, T, st, ms ? &ms1 : nullptr, false, &ovf, hist);
     if (s != THR_OK) return s;
     std::vector<uint32_t> redo;
     for (uint32_t q = 0; q < nq; ++q)
@@ -211,10 +213,23 @@ thr_status opt_profile(const thr_index* idx, uint32_t nq, const uint32_t* id_off
             K2[i] = K[q];
         }
         float ms2 = 0.f;
+        std::vector<unsigned long long> hist2;
         s = profile_pass(idx, uint32_t(redo.size()), off2.data(), ids2.data(), K2.data(),
-                         T2.data(), st, ms ? &ms2 : nullptr, true, nullptr);
+                         T2.data(), st, ms ? &ms2 : nullptr, true, nullptr,
+                         hist ? &hist2 : nullptr);
         if (s != THR_OK) return s;
         for (size_t i = 0; i < redo.size(); ++i) T[redo[i]] = T2[i];
+        if (hist) {  // the exact pass's bins replace those of the narrow one
+            std::vector<uint64_t> at(nq + 1, 0);
+            for (uint32_t q = 0; q < nq; ++q) at[q + 1] = at[q] + (id_off[q + 1] - id_off[q]) + 1;
+            uint64_t a2 = 0;
+            for (size_t i = 0; i < redo.size(); ++i) {
+                const uint32_t q = redo[i];
+                const uint64_t nb = at[q + 1] - at[q];
+                std::copy(hist2.begin() + a2, hist2.begin() + a2 + nb, hist->begin() + at[q]);
+                a2 += nb;
+            }
+        }
         ms1 += ms2;
     }
     if (ms) *ms = ms1;

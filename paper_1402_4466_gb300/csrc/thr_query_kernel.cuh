@@ -19,15 +19,19 @@ constexpr int kRows = kGW / 32;
 // flag << 62 | mixed flag << 63.
 constexpr int kMetaBatch = 32;  // mask records staged per round trip
 
-struct WarpSmem {
+// What every pass-A kernel keeps per warp (the staged kernel: only this).
+struct WarpCore {
     uint4 rec[kCH];
-    uint4 meta[kMetaBatch][4];     // mask records of kMetaBatch consecutive inputs
     unsigned long long tw[kGW];    // the subtile's result words, for the scan
     unsigned long long woff[kCH];  // stream offsets of the current query's ids
     uint32_t ids[kCH];             //   and the ids, when n <= kCH
     uint32_t qn, qT, qz, qoff;     // the current query: n, T, zmode, first id
     uint32_t qTx;                  //   largest threshold of its group (qT: the least)
     uint32_t qhi, qsym;            //   range bound and kind (QDesc)
+};
+// The direct kernels also stage mask records in shared memory.
+struct WarpSmem : WarpCore {
+    uint4 meta[kMetaBatch][4];     // mask records of kMetaBatch consecutive inputs
 };
 
 struct CtaSmem {
@@ -38,7 +42,7 @@ struct CtaSmem {
 // loads are cheap; keeping the values in registers would spill).  cached:
 // n <= kCH and ids / woff of WarpSmem hold its ids and their stream offsets.
 struct QView {
-    const volatile WarpSmem& w;
+    const volatile WarpCore& w;
     const uint32_t* all_ids;
     __device__ __forceinline__ uint32_t n() const { return w.qn; }
     __device__ __forceinline__ uint32_t T() const { return w.qT; }
@@ -638,7 +642,7 @@ __device__ __forceinline__ LocalScan local_scan(uint32_t x0, uint32_t x1, uint32
 // The warp's view of a query (or of a part of its inputs): n ids from
 // ids_off, its threshold and counting mode; ids and stream offsets are
 // cached in the warp's shared memory when n <= kCH.
-__device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, uint32_t ids_off,
+__device__ __forceinline__ void load_query(const PassAParams& p, WarpCore& ws, uint32_t ids_off,
                                            uint32_t n, uint32_t T, uint32_t zmode,
                                            uint32_t Tmax, uint32_t hi, uint32_t sym,
                                            uint32_t lane) {
@@ -665,7 +669,7 @@ __device__ __forceinline__ void load_query(const PassAParams& p, WarpSmem& ws, u
 // Re-encoding part 1 of a finished subtile: rows -> 4 consecutive words per
 // lane, local scan, the result words (unless one fill class) and the
 // aggregate to the slot's scratch.
-__device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws, uint32_t slot,
+__device__ __forceinline__ void store_subtile(const PassAParams& p, WarpCore& ws, uint32_t slot,
                                               uint32_t g, uint32_t x0, uint32_t x1,
                                               uint32_t lane, const uint64_t (&orow)[kRows]) {
     const uint64_t sg = uint64_t(slot) * p.NG + g;
@@ -704,7 +708,7 @@ __device__ __forceinline__ void store_subtile(const PassAParams& p, WarpSmem& ws
 // lower the occupancy) of the single-query path that shares the kernel;
 // used for counters of 7 bits and more (Count::kInlineGroups).
 template <class Count>
-__device__ __noinline__ void finish_group(const PassAParams& p, WarpSmem& ws, uint2 grp,
+__device__ __noinline__ void finish_group(const PassAParams& p, WarpCore& ws, uint2 grp,
                                           uint32_t g, uint32_t x0, uint32_t x1, uint32_t lane,
                                           uint32_t k_ones, uint32_t d_act, Count* count) {
     for (uint32_t i = 0; i < grp.y; ++i) {

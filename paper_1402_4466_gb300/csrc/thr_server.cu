@@ -230,7 +230,8 @@ thr_status thr_server_create(const thr_index* idx, uint32_t workers, uint32_t ma
 thr_status thr_server_submit(thr_server* s, const uint32_t* ids, uint32_t n, uint32_t T,
                              uint64_t* ticket) {
     if (!s || !ids || !ticket) return report_error(THR_E_INVAL, "null argument");
-    if (n == 0 || n > 65536) return report_error(THR_E_INVAL, "n must be in 1..65536");
+    if (n == 0 || n > THR_MAX_IDS)
+        return report_error(THR_E_INVAL, "n must be in 1..THR_MAX_IDS (2^20 - 1)");
     for (uint32_t i = 0; i < n; ++i)
         if (ids[i] >= s->idx->nbitmaps) return report_error(THR_E_INVAL, "id out of range");
     Request* r = new (std::nothrow) Request;

@@ -10,6 +10,17 @@ touches O(1) words at each seam.
 
     sh = ShardedIndex(words, offsets, r, rank, world)   # builds the local index
     out = sh.query(ids, T)                              # on every rank
+    T, out = sh.query_opt(ids, K)                       # opt-threshold over all rows
+
+An opt-threshold query (the largest T whose result holds at least K rows)
+over row shards needs one more exchange: each shard's profiling pass gives
+its own answer T_g and its count histogram, exact at or above T_g
+(thr_query_opt_hist); the histograms are summed and the largest T_g taken
+across ranks (all-reduce), which fixes T for the whole (`combine_opt`), and
+then every shard answers the threshold query at that T.
+
+`ShardSet` runs every shard in one process (the same arithmetic, the
+exchange replaced by lists): the way to test the sharded path on one GPU.
 """
 from __future__ import annotations
 
@@ -43,6 +54,49 @@ def slice_index(words, offsets, r: int, row0: int, rows: int):
     return np.concatenate(parts), off
 
 
+def combine_opt(hists, Ts, K: int) -> int:
+    """The opt-threshold answer for K over all shards, from each shard's
+    answer T_g and count histogram (exact for counts >= max(T_g, 1)): the
+    first c from n down to max(max_g T_g, 1) whose summed suffix reaches K,
+    else 0.  The whole's answer is at least every T_g (a shard's K rows are
+    rows of the whole), so only bins that every shard has exactly are read."""
+    total = np.sum(np.stack([np.asarray(h, dtype=np.uint64) for h in hists]), axis=0)
+    lo = max(max(int(t) for t in Ts), 1)
+    suffix = 0
+    for c in range(len(total) - 1, lo - 1, -1):
+        suffix += int(total[c])
+        if suffix >= K:
+            return c
+    return 0
+
+
+class ShardSet:
+    """Every row shard of an index in this process, on the current GPU:
+    query() answers each shard and stitches the results, query_opt() combines
+    the shards' histograms first (no collective: the exchange is a list)."""
+
+    def __init__(self, words, offsets, r: int, shards: int):
+        self.r = int(r)
+        self.ranges = shard_ranges(r, shards)
+        self.idx = []
+        for row0, rows in self.ranges:
+            w, o = slice_index(words, offsets, r, row0, rows)
+            self.idx.append(thr.idx_build_rle(w, o, rows))
+
+    def close(self):
+        for g in self.idx:
+            g.close()
+
+    def query(self, ids, T: int) -> np.ndarray:
+        parts = [thr.thr_query(g, ids, T) for g in self.idx]
+        return thr.thr_rle_stitch(parts, [rows for _, rows in self.ranges])
+
+    def query_opt(self, ids, K: int = 1):
+        got = [thr.thr_query_opt_hist(g, ids, K) for g in self.idx]
+        T = combine_opt([h for _, h in got], [t for t, _ in got], K)
+        return T, self.query(ids, T)
+
+
 class ShardedIndex:
     """The rank's shard of a row-sharded index.  `local_query(ids, T)` may
     replace the GPU query of the shard (it must return the shard's result
@@ -57,6 +111,28 @@ class ShardedIndex:
         self.rows = rows
         self.idx = thr.idx_build_rle(self.words, self.offsets, rows) if build_index else None
         self.local_query = local_query or (lambda ids, T: thr.thr_query(self.idx, ids, T))
+
+    def query_opt(self, ids, K: int = 1, group=None, local_hist=None):
+        """(T, result) of the opt-threshold query over all rows: the shards'
+        histograms summed (all-reduce) and their answers' maximum, combined
+        by combine_opt, then the threshold query at T on every shard.
+        local_hist(ids, K) -> (T_g, hist) may replace the shard's profiling
+        pass (thr_query_opt_hist)."""
+        import torch
+        import torch.distributed as dist
+        if local_hist is None:
+            T_g, hist = thr.thr_query_opt_hist(self.idx, ids, K)
+        else:
+            T_g, hist = local_hist(ids, K)
+        if self.world == 1:
+            T = combine_opt([hist], [T_g], K)
+        else:
+            h = torch.from_numpy(np.asarray(hist, dtype=np.uint64).astype(np.int64))
+            t = torch.tensor([int(T_g)], dtype=torch.int64)
+            dist.all_reduce(h, op=dist.ReduceOp.SUM, group=group)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+            T = combine_opt([h.numpy().astype(np.uint64)], [int(t.item())], K)
+        return T, self.query(ids, T, group=group)
 
     def query(self, ids, T: int, group=None) -> np.ndarray:
         import torch.distributed as dist

@@ -138,3 +138,30 @@ def test_checks_kill_opt_mutants(tmp_path, name, old, new):
             if T != T_bf or _rows(s, r) != set(np.nonzero(count >= T_bf)[0].tolist()):
                 return  # killed
     pytest.fail(f"mutant '{name}' survived")
+
+
+def test_count_histogram_brute_force_and_threshold_sizes():
+    """The count histogram against per-row counts from the uncompressed bits
+    (brute force) and, by suffix sums, against the sizes of the threshold
+    oracle's results; bins add up over row shards cut at any word boundary."""
+    rng = np.random.default_rng(93)
+    for _ in range(25):
+        n = int(rng.integers(1, 8))
+        r = int(rng.choice([1, 5, 63, 64, 65, 130, 400, 1000]))
+        bitsets = oracle_pins.random_bitsets(rng, n, r)
+        o, words = _index(bitsets, r)
+        ids = rng.integers(0, n, int(rng.integers(1, 2 * n + 1))).tolist()
+        hist = o.count_histogram(ids)
+        want = np.bincount(_counts(bitsets, ids, r), minlength=len(ids) + 1)
+        assert hist.tolist() == want.tolist()
+        for T in range(0, len(ids) + 2):
+            size = len(_rows(o.threshold(ids, T), r))
+            assert size == int(hist[T:].sum())
+        W = (r + 63) // 64
+        if W >= 2:
+            cut = int(rng.integers(1, W))
+            lo = [oracle.encode(w[:cut], 64 * cut) for w in words]
+            hi = [oracle.encode(w[cut:], r - 64 * cut) for w in words]
+            h = (oracle.Index(lo, 64 * cut).count_histogram(ids) +
+                 oracle.Index(hi, r - 64 * cut).count_histogram(ids))
+            assert h.tolist() == hist.tolist()

@@ -79,7 +79,39 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, r, seed, queries, out_dir):
+def _partial_hist(ix, ids, K):
+    """A shard's answer and its count histogram as the GPU profiling pass
+    gives them: exact for counts >= max(T, 1), bins below that (and bin 0)
+    not computed (zero here)."""
+    T, _ = ix.opt_threshold(ids, K)
+    h = ix.count_histogram(ids).copy()
+    h[: max(T, 1)] = 0
+    return T, h
+
+
+def test_opt_threshold_over_shards_combines_histograms():
+    r = 200_000 + 3
+    arrays = _bitmaps(11, 10, r)
+    streams = [oracle.encode(a, r) for a in arrays]
+    words, offsets = oracle.concat(streams)
+    whole = oracle.Index(streams, r)
+    for world in (2, 3, 5):
+        shards = []
+        for row0, rows in sharded.shard_ranges(r, world):
+            sw, so = sharded.slice_index(words, offsets, r, row0, rows)
+            shards.append((oracle.Index([sw[int(so[i]):int(so[i + 1])] for i in range(10)],
+                                        rows), rows))
+        for ids in ([0, 1, 2, 3], list(range(10)), [1, 1, 4, 8, 8], [3]):
+            for K in (1, 7, 1000, r // 3, r, r + 1):
+                got = [_partial_hist(ix, ids, K) for ix, _ in shards]
+                T = sharded.combine_opt([h for _, h in got], [t for t, _ in got], K)
+                Tw, want = whole.opt_threshold(ids, K)
+                assert T == Tw, (world, ids, K)
+                parts = [ix.threshold(ids, T) for ix, _ in shards]
+                assert np.array_equal(thr.thr_rle_stitch(parts, [n for _, n in shards]), want)
+
+
+def _rank_main(rank, world, port, r, seed, queries, out_dir, opt_queries=()):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -94,6 +126,9 @@ def _rank_main(rank, world, port, r, seed, queries, out_dir):
                               local_query=lambda ids, T: local.threshold(ids, T),
                               build_index=False)
     results = [sh.query(ids, T) for ids, T in queries]
+    for ids, K in opt_queries:
+        T, res = sh.query_opt(ids, K, local_hist=lambda i, k: _partial_hist(local, i, k))
+        results += [np.array([T], np.uint64), res]
     np.savez(os.path.join(out_dir, f"rank{rank}.npz"), *results)
     dist.barrier()
     dist.destroy_process_group()
@@ -103,12 +138,18 @@ def test_two_gloo_ranks_agree_with_the_oracle(tmp_path):
     import torch.multiprocessing as mp
     r = 130_000 + 5
     queries = [([0, 1, 2, 3, 4], 2), (list(range(10)), 3), ([1, 1, 4, 8], 2), ([2, 6], 2)]
+    opt_queries = [(list(range(10)), 1), ([0, 1, 2, 3, 4], 500), ([1, 1, 4, 8], 40_000)]
     port = _free_port()
-    mp.start_processes(_rank_main, args=(2, port, r, 7, queries, str(tmp_path)), nprocs=2,
-                       join=True, start_method="spawn")
+    mp.start_processes(_rank_main, args=(2, port, r, 7, queries, str(tmp_path), opt_queries),
+                       nprocs=2, join=True, start_method="spawn")
     arrays = _bitmaps(7, 10, r)
     whole = oracle.Index([oracle.encode(a, r) for a in arrays], r)
     for rank in range(2):
         got = np.load(os.path.join(tmp_path, f"rank{rank}.npz"))
         for k, (ids, T) in enumerate(queries):
             assert np.array_equal(got[f"arr_{k}"], whole.threshold(ids, T))
+        for j, (ids, K) in enumerate(opt_queries):
+            T, want = whole.opt_threshold(ids, K)
+            k = len(queries) + 2 * j
+            assert int(got[f"arr_{k}"][0]) == T, (ids, K)
+            assert np.array_equal(got[f"arr_{k + 1}"], want)
