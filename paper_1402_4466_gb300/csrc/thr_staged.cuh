@@ -309,7 +309,10 @@ __device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, co
     u.c0 = c0;
     u.nrec = 0;
     u.fill = 0;
-    if (it >= p.nlist * p.NG) return u;
+    if (it >= p.nlist * p.NG) {  // no more work
+        u.flags = 0;
+        return u;
+    }
     uint32_t li, g;
     if (p.order) {
         g = it / p.nlist;
