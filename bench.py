@@ -66,7 +66,7 @@ def parse():
                     help="build the workload, run one warm-up query at threshold T and "
                          "then one more (the launch to capture with a profiler); no timing")
     ap.add_argument("--variant", default="csa",
-                    choices=["csa", "direct", "position", "scancount", "looped"],
+                    choices=["csa", "staged", "position", "scancount", "looped"],
                     help="counting variant of --profile-query")
     ap.add_argument("--batch", action="store_true",
                     help="with --profile-query: the step's four thresholds as one batched "
@@ -305,7 +305,7 @@ def run_ours(args):
     plain_value = len(q_ms) / (sum(q_ms) / 1e3)
     plain_results = {T: thr.thr_query(idx, ids, T) for T in Ts}
     variant_ms = {}
-    for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("direct", thr.THR_VARIANT_DIRECT),
+    for vname, vflag in (("csa", thr.THR_VARIANT_CSA), ("staged", thr.THR_VARIANT_STAGED),
                          ("position", thr.THR_VARIANT_POSITION),
                          ("scancount", thr.THR_VARIANT_SCANCOUNT)):
         per_t = {}
@@ -588,7 +588,7 @@ def profile_query(args):
     torch.cuda.init()
     r, gw, goff = make_index_inputs(args.seed)
     idx = thr.idx_build_rle(gw, goff, r)
-    flag = {"csa": thr.THR_VARIANT_CSA, "direct": thr.THR_VARIANT_DIRECT,
+    flag = {"csa": thr.THR_VARIANT_CSA, "staged": thr.THR_VARIANT_STAGED,
             "position": thr.THR_VARIANT_POSITION,
             "scancount": thr.THR_VARIANT_SCANCOUNT, "looped": thr.THR_VARIANT_LOOPED}[args.variant]
     ids = np.arange(synth.MANY_N, dtype=np.uint32)

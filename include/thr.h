@@ -40,7 +40,7 @@
  * A CUDA failure returns THR_E_CUDA.  No kernel of the library waits on
  * another CTA or launch (cross-CTA scans finish in the last CTA to arrive).
  * The one device-side wait is a warp's wait for its own bulk copies into
- * shared memory (THR_VARIANT_CSA); it gives up after about a second, and the
+ * shared memory (THR_VARIANT_STAGED); it gives up after about a second, and the
  * call then returns THR_E_TIMEOUT (the results are not valid).
  */
 #ifndef THR_H
@@ -82,10 +82,7 @@ typedef enum {
  *                          (default; any n and T), inputs decoded four at a
  *                          time; when T is close to n the zeros of the
  *                          active inputs are counted instead, which needs
- *                          fewer counter bits.  Each input's compressed
- *                          words for a 128-word subtile are first copied to
- *                          shared memory by bulk copies, several inputs
- *                          ahead of the adds
+ *                          fewer counter bits
  *   THR_VARIANT_POSITION   the same counters counting ones; inputs that mix
  *                          fills and literals inside a 128-word subtile are
  *                          decoded position by position (each lane walks the
@@ -104,15 +101,17 @@ typedef enum {
  *                          far, each input one AND-OR per level; used when
  *                          1 <= T <= 4 and T <= n, else CSA runs.  Not an arm
  *                          of the rule or learned policies.
- *   THR_VARIANT_DIRECT     THR_VARIANT_CSA without the shared-memory copies:
- *                          every word is loaded from global memory where it
- *                          is added (for comparison; not a policy arm) */
+ *   THR_VARIANT_STAGED     THR_VARIANT_CSA with each input's compressed words
+ *                          for a 128-word subtile first copied to shared
+ *                          memory by bulk copies, the next inputs' copies in
+ *                          flight while the current ones are added (not a
+ *                          policy arm) */
 #define THR_VARIANT_CSA 0x000u
 #define THR_VARIANT_SCANCOUNT 0x200u
 #define THR_VARIANT_POSITION 0x400u
 #define THR_VARIANT_SPLIT 0x600u
 #define THR_VARIANT_LOOPED 0x800u
-#define THR_VARIANT_DIRECT 0xA00u
+#define THR_VARIANT_STAGED 0xA00u
 #define THR_VARIANT_MASK 0xE00u
 
 /*

@@ -32,7 +32,7 @@ THR_SYM_ODD = 0x4000
 THR_VARIANT_CSA, THR_VARIANT_SCANCOUNT, THR_VARIANT_POSITION = 0x000, 0x200, 0x400
 THR_VARIANT_SPLIT = 0x600
 THR_VARIANT_LOOPED = 0x800
-THR_VARIANT_DIRECT = 0xA00
+THR_VARIANT_STAGED = 0xA00
 THR_MAX_IDS = 1048575  # bitmap ids (with repeats) per query: 2^20 - 1
 THR_VARIANT_MASK = 0xE00
 

@@ -130,41 +130,41 @@ thr_status report_error(thr_status st, const char* msg) { return fail(st, "%s", 
 
 const KernelEntry* kernel_table(int* count) {
     static const KernelEntry tab[] = {
-        {1, launch_staged_1, occupancy_staged_1, launch_threshold_1,
-         occupancy_threshold_1, launch_threshold_pos_1,
+        {1, launch_threshold_1, occupancy_threshold_1, launch_staged_1,
+         occupancy_staged_1, launch_threshold_pos_1,
          occupancy_threshold_pos_1, launch_split_1, occupancy_split_1},
-        {2, launch_staged_2, occupancy_staged_2, launch_threshold_2,
-         occupancy_threshold_2, launch_threshold_pos_2,
+        {2, launch_threshold_2, occupancy_threshold_2, launch_staged_2,
+         occupancy_staged_2, launch_threshold_pos_2,
          occupancy_threshold_pos_2, launch_split_2, occupancy_split_2},
-        {3, launch_staged_3, occupancy_staged_3, launch_threshold_3,
-         occupancy_threshold_3, launch_threshold_pos_3,
+        {3, launch_threshold_3, occupancy_threshold_3, launch_staged_3,
+         occupancy_staged_3, launch_threshold_pos_3,
          occupancy_threshold_pos_3, launch_split_3, occupancy_split_3},
-        {4, launch_staged_4, occupancy_staged_4, launch_threshold_4,
-         occupancy_threshold_4, launch_threshold_pos_4,
+        {4, launch_threshold_4, occupancy_threshold_4, launch_staged_4,
+         occupancy_staged_4, launch_threshold_pos_4,
          occupancy_threshold_pos_4, launch_split_4, occupancy_split_4},
-        {5, launch_staged_5, occupancy_staged_5, launch_threshold_5,
-         occupancy_threshold_5, launch_threshold_pos_5,
+        {5, launch_threshold_5, occupancy_threshold_5, launch_staged_5,
+         occupancy_staged_5, launch_threshold_pos_5,
          occupancy_threshold_pos_5, launch_split_5, occupancy_split_5},
-        {6, launch_staged_6, occupancy_staged_6, launch_threshold_6,
-         occupancy_threshold_6, launch_threshold_pos_6,
+        {6, launch_threshold_6, occupancy_threshold_6, launch_staged_6,
+         occupancy_staged_6, launch_threshold_pos_6,
          occupancy_threshold_pos_6, launch_split_6, occupancy_split_6},
-        {7, launch_staged_7, occupancy_staged_7, launch_threshold_7,
-         occupancy_threshold_7, launch_threshold_pos_7,
+        {7, launch_threshold_7, occupancy_threshold_7, launch_staged_7,
+         occupancy_staged_7, launch_threshold_pos_7,
          occupancy_threshold_pos_7, launch_split_7, occupancy_split_7},
-        {8, launch_staged_8, occupancy_staged_8, launch_threshold_8,
-         occupancy_threshold_8, launch_threshold_pos_8,
+        {8, launch_threshold_8, occupancy_threshold_8, launch_staged_8,
+         occupancy_staged_8, launch_threshold_pos_8,
          occupancy_threshold_pos_8, launch_split_8, occupancy_split_8},
-        {10, launch_staged_10, occupancy_staged_10, launch_threshold_10,
-         occupancy_threshold_10, launch_threshold_pos_10,
+        {10, launch_threshold_10, occupancy_threshold_10, launch_staged_10,
+         occupancy_staged_10, launch_threshold_pos_10,
          occupancy_threshold_pos_10, nullptr, nullptr},
-        {12, launch_staged_12, occupancy_staged_12, launch_threshold_12,
-         occupancy_threshold_12, launch_threshold_pos_12,
+        {12, launch_threshold_12, occupancy_threshold_12, launch_staged_12,
+         occupancy_staged_12, launch_threshold_pos_12,
          occupancy_threshold_pos_12, nullptr, nullptr},
-        {16, launch_staged_16, occupancy_staged_16, launch_threshold_16,
-         occupancy_threshold_16, launch_threshold_pos_16,
+        {16, launch_threshold_16, occupancy_threshold_16, launch_staged_16,
+         occupancy_staged_16, launch_threshold_pos_16,
          occupancy_threshold_pos_16, nullptr, nullptr},
-        {20, launch_staged_20, occupancy_staged_20, launch_threshold_20,
-         occupancy_threshold_20, launch_threshold_pos_20,
+        {20, launch_threshold_20, occupancy_threshold_20, launch_staged_20,
+         occupancy_staged_20, launch_threshold_pos_20,
          occupancy_threshold_pos_20, nullptr, nullptr},
     };
     *count = int(sizeof tab / sizeof tab[0]);

@@ -42,7 +42,7 @@ cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t s
         case 2: return tab[w].launch_pos(p, grid, st);
         case 3: return tab[w].launch_split ? tab[w].launch_split(p, grid, st)
                                            : cudaErrorInvalidValue;
-        case 5: return tab[w].launch_direct(p, grid, st);
+        case 5: return tab[w].launch_staged(p, grid, st);
         default: return tab[w].launch(p, grid, st);
     }
 }
@@ -114,8 +114,8 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
         return;
     }
     choose_class(n, T, cls, zmode);
-    if (v == kVarDirect) {
-        *cls += kClassDirect;
+    if (v == kVarStaged) {
+        *cls += kClassStaged;
         return;
     }
     if (v == kVarSplit) {
@@ -150,7 +150,7 @@ cudaError_t class_occupancy(int cls, int* per_sm) {
         case 2: return tab[w].occupancy_pos(per_sm);
         case 3: return tab[w].occupancy_split ? tab[w].occupancy_split(per_sm)
                                               : cudaErrorInvalidValue;
-        case 5: return tab[w].occupancy_direct(per_sm);
+        case 5: return tab[w].occupancy_staged(per_sm);
         default: return tab[w].occupancy(per_sm);
     }
 }

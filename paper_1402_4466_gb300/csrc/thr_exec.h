@@ -14,13 +14,13 @@
 namespace thr {
 
 // Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
-// kernel_table()[c].S (staged inputs, grouped decode), kClassScanCount the
+// kernel_table()[c].S (grouped decode), kClassScanCount the
 // ScanCount kernel, kClassPos + c carry-save of width kernel_table()[c].S
 // with the position-major decode of mixed inputs, kClassSplit + c carry-save
 // with the inputs split among the CTA's warps (widths up to kSplitWidths),
 // kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax),
-// kClassDirect + c carry-save of width kernel_table()[c].S loading every
-// word from global memory (the grouped decode without staging).
+// kClassStaged + c carry-save of width kernel_table()[c].S with each input's
+// words staged in shared memory by bulk copies (thr_staged.cuh).
 constexpr int kNumWidths = 12;
 constexpr int kSplitWidths = 8;  // S = 1..8
 constexpr int kLoopedMax = 4;    // Looped levels (thresholds) instantiated
@@ -28,11 +28,11 @@ constexpr int kClassScanCount = kNumWidths;
 constexpr int kClassPos = kNumWidths + 1;
 constexpr int kClassSplit = 2 * kNumWidths + 1;
 constexpr int kClassLooped = kClassSplit + kSplitWidths;
-constexpr int kClassDirect = kClassLooped + kLoopedMax;
-constexpr int kNumClasses = kClassDirect + kNumWidths;
+constexpr int kClassStaged = kClassLooped + kLoopedMax;
+constexpr int kNumClasses = kClassStaged + kNumWidths;
 static_assert(kNumClasses <= 64, "class sets are 64-bit masks");
-// Family of a class: 0 staged carry-save, 1 ScanCount, 2 position-major,
-// 3 split inputs, 4 Looped, 5 direct carry-save.
+// Family of a class: 0 grouped carry-save, 1 ScanCount, 2 position-major,
+// 3 split inputs, 4 Looped, 5 staged carry-save.
 constexpr int kNumFamilies = 6;
 inline int class_family(int c) {
     return c < kNumWidths
@@ -40,7 +40,7 @@ inline int class_family(int c) {
                : (c == kClassScanCount
                       ? 1
                       : (c < kClassSplit ? 2
-                                         : (c < kClassLooped ? 3 : (c < kClassDirect ? 4 : 5))));
+                                         : (c < kClassLooped ? 3 : (c < kClassStaged ? 4 : 5))));
 }
 // Counter-width index of a carry-save class (levels - 1 for Looped).
 inline int class_width(int c) {
@@ -49,8 +49,8 @@ inline int class_width(int c) {
                : (c < kClassSplit
                       ? c - kClassPos
                       : (c < kClassLooped ? c - kClassSplit
-                                          : (c < kClassDirect ? c - kClassLooped
-                                                              : c - kClassDirect)));
+                                          : (c < kClassStaged ? c - kClassLooped
+                                                              : c - kClassStaged)));
 }
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
@@ -122,10 +122,10 @@ constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2, kVarSplit = 3;
 constexpr int kNumVariants = 4;  // the policies' choices
 //   kVarLooped     Looped levels (Sec. 6.2) for 1 <= T <= kLoopedMax, T <= n
 //                  (else kVarCsa runs); chosen by flag only
-//   kVarDirect     kVarCsa without staging: every word loaded from global
-//                  memory where it is added; chosen by flag only
+//   kVarStaged     kVarCsa with each input's words copied to shared memory
+//                  by bulk copies ahead of the adds; chosen by flag only
 constexpr int kVarLooped = 4;
-constexpr int kVarDirect = 5;
+constexpr int kVarStaged = 5;
 // Kernel class and zero counting of a query run with variant v.
 void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode);
 

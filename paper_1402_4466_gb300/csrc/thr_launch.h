@@ -13,10 +13,10 @@ using OccupancyFn = cudaError_t (*)(int* blocks_per_sm);
 
 struct KernelEntry {
     int S;
-    LaunchFn launch;          // staged inputs (thr_staged.cuh), grouped decode
+    LaunchFn launch;          // grouped decode, every word loaded from global memory
     OccupancyFn occupancy;
-    LaunchFn launch_direct;   // grouped decode loading every word from global memory
-    OccupancyFn occupancy_direct;
+    LaunchFn launch_staged;   // staged inputs (thr_staged.cuh)
+    OccupancyFn occupancy_staged;
     LaunchFn launch_pos;      // position-major decode of mixed inputs
     OccupancyFn occupancy_pos;
     LaunchFn launch_split;    // inputs split among the CTA's warps (S <= 8), or null

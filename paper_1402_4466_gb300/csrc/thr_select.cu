@@ -110,7 +110,7 @@ int variant_of_flag(uint32_t f) {
         case THR_VARIANT_SCANCOUNT: return kVarScanCount;
         case THR_VARIANT_SPLIT: return kVarSplit;
         case THR_VARIANT_LOOPED: return kVarLooped;
-        case THR_VARIANT_DIRECT: return kVarDirect;
+        case THR_VARIANT_STAGED: return kVarStaged;
         default: return -1;
     }
 }

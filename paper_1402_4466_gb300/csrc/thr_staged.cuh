@@ -1,4 +1,4 @@
-// Pass A with staged inputs (k_staged<S>): the default carry-save kernel.
+// Pass A with staged inputs (k_staged<S>, THR_VARIANT_STAGED): carry-save counting fed by bulk copies.
 //
 // The counting and the re-encoding are those of k_threshold<S>
 // (thr_query_kernel.cuh); what changes is how an input's words reach the

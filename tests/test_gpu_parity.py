@@ -306,7 +306,7 @@ def test_split_many_criteria_full_size(many_criteria_full):
         p.check(list(range(synth.MANY_N)), T, SPLIT)
 
 
-# ---- the default kernel's staged copies: stream segments that start at odd
+# ---- the staged kernel's copies: stream segments that start at odd
 #      and even stream words, sparse inputs packed several to a ring slot,
 #      and the last words of the index
 
@@ -331,30 +331,31 @@ def test_staged_segments_alignment_and_index_end():
     p = Pair(arrays, r)
     n = len(arrays)
     for T in (1, 2, 3, 4, 5, 7, n):
-        p.check(list(range(n)), T)
-        p.check(list(range(n))[::-1] + [n - 1, 0], T)
+        for flags in (0, thr.THR_VARIANT_STAGED):
+            p.check(list(range(n)), T, flags)
+            p.check(list(range(n))[::-1] + [n - 1, 0], T, flags)
 
 
-# ---- the grouped carry-save decode loading every word from global memory
+# ---- the staged carry-save kernel (inputs copied to shared memory first)
 
-DIRECT = thr.THR_VARIANT_DIRECT
+STAGED = thr.THR_VARIANT_STAGED
 
 
-def test_direct_random_tiny_all_thresholds():
+def test_staged_random_tiny_all_thresholds():
     rng = np.random.default_rng(505)
     for _ in range(20):
         n = int(rng.integers(1, 13))
         r = int(rng.choice([1, 63, 64, 65, 1000, 4096, 9000, 40000]))
         p = from_ints(oracle_pins.random_bitsets(rng, n, r), r)
         for T in range(0, n + 2):
-            p.check(list(range(n)), T, DIRECT)
+            p.check(list(range(n)), T, STAGED)
 
 
-def test_direct_many_criteria_full_size(many_criteria_full):
+def test_staged_many_criteria_full_size(many_criteria_full):
     words, r = many_criteria_full
     p = Pair(words, r)
     for T in (*synth.MANY_TS, 1, 64):
-        p.check(list(range(synth.MANY_N)), T, DIRECT)
+        p.check(list(range(synth.MANY_N)), T, STAGED)
 
 
 # ---- the Looped levels (Algorithm 3, Sec. 6.2) for T <= 4
@@ -451,8 +452,8 @@ def test_lost_copy_returns_timeout_and_context_survives(monkeypatch):
     dense = [oracle_pins.mask(r) & int(x) for x in (0x5555 << 8, 0xF0F0F0F0F0F0F0F0F0F0)]
     q = from_ints(dense + [oracle_pins.mask(r) & 0x123456789ABCDEF], r)
     with pytest.raises(thr.ThrError) as e:
-        thr.thr_query(q.g, [0, 1, 2], 2)
+        thr.thr_query(q.g, [0, 1, 2], 2, flags=thr.THR_VARIANT_STAGED)
     assert e.value.status == thr.THR_E_TIMEOUT
     monkeypatch.delenv("THR_TEST_LOST_COPY")
-    q.check([0, 1, 2], 2)
-    p.check([0, 1, 2], 2)
+    q.check([0, 1, 2], 2, thr.THR_VARIANT_STAGED)
+    p.check([0, 1, 2], 2, thr.THR_VARIANT_STAGED)
