@@ -40,10 +40,15 @@ static_assert(kWaveBytes <= (1 << 12), "wave offsets take 12 bits");
 
 struct StageWarp {
     alignas(16) unsigned char buf[2][kWaveBytes];
+    // a mixed input's literals are scattered into its tile (one per input of
+    // a group of kGroup) at their subtile words, then read back row by row
+    unsigned long long tile[kGroup][kGW];
     unsigned long long bar[2];  // one mbarrier per buffer
     // [unit parity][record]: byte offset of the record's words in its wave's
     // buffer | first word odd << 12 | mixed << 13 | has ones-fill words << 14
+    // | first position byte's offset in its 16-byte unit << 15 | words << 19
     uint32_t dir[2][kCH];
+    uint32_t psum[kCH];  // bytes the unit's records take in waves, inclusive prefix
 };
 struct StagedCta {
     WarpCore w[kNW];
@@ -146,44 +151,42 @@ __device__ __forceinline__ uint32_t wave_end(uint32_t w, uint32_t b) {
     return (w >> (16 * b + 8)) & 0xFFu;
 }
 
-// Send the unit's next records, as many as fit buffer b, as one wave:
-// offsets by a scan of their sizes (dir), one arrive with the wave's bytes,
-// then the copies (lane per record).  `waves` receives the wave's records.
+// Bytes a record takes in a wave, in 16-byte units: a literal run its
+// words; a mixed input its words, their position bytes and, with ones-fill
+// words, the 16-byte ones mask of its mask record.
+__device__ __forceinline__ uint32_t data_bytes(uint32_t len, uint32_t odd) {
+    return (8u * (len + odd) + 15u) & ~15u;
+}
+__device__ __forceinline__ uint32_t pos_bytes(uint32_t len, uint32_t mis) {
+    return (mis + len + 15u) & ~15u;
+}
+__device__ __forceinline__ uint32_t record_bytes(const uint4& rec) {
+    const uint32_t len = (rec.y >> 8) & 0x1FFu;
+    uint32_t b = data_bytes(len, rec.x & 1u);
+    if (rec.y >> 31) b += pos_bytes(len, rec.x & 15u) + (((rec.y >> 30) & 1u) ? 16u : 0u);
+    return b;
+}
+
+// Send the unit's next records, as many as fit buffer b, as one wave: the
+// wave's end from the bytes prefix (psum), one arrive with the wave's bytes,
+// then the copies (lane per record) and the records' dir entries.  `waves`
+// receives the wave's records.
 __device__ __forceinline__ void issue_wave(const PassAParams& p, const WarpCore& ws,
                                            StageWarp& sw, Unit& u, uint32_t b, uint32_t lane,
                                            uint32_t& waves) {
     const uint32_t par = (u.flags >> 3) & 1u;
     uint32_t* dir = sw.dir[par];
     const uint32_t r0 = u.fill;
-    uint32_t used = 0, r = r0;
-    while (r < u.nrec) {  // offsets, 32 records at a time
+    const uint32_t start = r0 ? sw.psum[r0 - 1] : 0u;
+    uint32_t r = r0;
+    while (r < u.nrec) {  // the records that fit, 32 at a time
         const uint32_t j = r + lane;
-        uint32_t size = 0, odd = 0, mixed = 0, ones = 0;
-        if (j < u.nrec) {
-            const uint4 rec = ws.rec[j];
-            const uint32_t len = (rec.y >> 8) & 0x1FFu;
-            odd = rec.x & 1u;
-            mixed = rec.y >> 31;
-            ones = (rec.y >> 30) & 1u;
-            size = ((8u * (len + odd) + 15u) & ~15u) + (mixed ? uint32_t(sizeof(MaskRec)) : 0u);
-        }
-        uint32_t incl = size;
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            const uint32_t t = __shfl_up_sync(~0u, incl, dd);
-            if (lane >= uint32_t(dd)) incl += t;
-        }
-        const bool fits = j < u.nrec && used + incl <= uint32_t(kWaveBytes);
+        const bool fits = j < u.nrec && sw.psum[j] - start <= uint32_t(kWaveBytes);
         const uint32_t m = __popc(__ballot_sync(~0u, fits));
-        if (fits) {
-            const uint32_t off = used + incl - size + (mixed ? uint32_t(sizeof(MaskRec)) : 0u);
-            dir[j] = off | (odd << 12) | (mixed << 13) | (ones << 14);
-        }
-        if (m) used += __shfl_sync(~0u, incl, m - 1);
         r += m;
         if (m < 32) break;
     }
-    __syncwarp();
+    const uint32_t used = sw.psum[r - 1] - start;  // r > r0: one record always fits
     const uint32_t bar = smem_addr(&sw.bar[b]);
     fence_proxy_async();
     if (lane == 0) mbar_arrive_expect_tx(bar, used + (p.lose ? 16u : 0u));
@@ -191,68 +194,86 @@ __device__ __forceinline__ void issue_wave(const PassAParams& p, const WarpCore&
     unsigned char* base = sw.buf[b];
     for (uint32_t j = r0 + lane; j < r; j += 32) {  // the copies
         const uint4 rec = ws.rec[j];
-        const uint32_t e = dir[j];
         const uint64_t seg = (uint64_t(rec.y & 0xFFu) << 32) | rec.x;
         const uint32_t len = (rec.y >> 8) & 0x1FFu;
-        const uint32_t off = e & 0xFFFu;
-        if (rec.y >> 31)
-            bulk_copy(smem_addr(base + off - sizeof(MaskRec)),
-                      p.masks + ((uint64_t(rec.w) << 32) | rec.z), uint32_t(sizeof(MaskRec)), bar);
-        bulk_copy(smem_addr(base + off), p.words + (seg & ~1ull),
-                  (8u * (len + (rec.x & 1u)) + 15u) & ~15u, bar);
+        const uint32_t odd = rec.x & 1u, mixed = rec.y >> 31, ones = (rec.y >> 30) & 1u;
+        const uint32_t mis = rec.x & 15u;
+        uint32_t off = sw.psum[j] - start - record_bytes(rec);
+        if (ones) {  // the ones mask: bytes 32 .. 47 of the mask record
+            bulk_copy(smem_addr(base + off),
+                      reinterpret_cast<const unsigned char*>(
+                          p.masks + ((uint64_t(rec.w) << 32) | rec.z)) + 32,
+                      16u, bar);
+            off += 16u;
+        }
+        const uint32_t db = data_bytes(len, odd);
+        bulk_copy(smem_addr(base + off), p.words + (seg & ~1ull), db, bar);
+        if (mixed)
+            bulk_copy(smem_addr(base + off + db), p.spos + (seg & ~15ull), pos_bytes(len, mis),
+                      bar);
+        dir[j] = off | (odd << 12) | (mixed << 13) | (ones << 14) | (mis << 15) | (len << 19);
     }
+    __syncwarp();
     waves = (waves & ~(0xFFFFu << (16 * b))) | ((r0 | (r << 8)) << (16 * b));
     u.fill = r;
 }
 
 // Values of records r0 .. r0 + kGroup - 1 (< rend) at the lane's words
-// x0 + 32 r + lane, from the wave buffer: a literal run row by row, a mixed
-// input through its mask record (the literal at segment word pre[r] +
-// popc(cm[r] below the lane); a ones-fill word from the ones mask; else 0).
+// x0 + 32 r + lane, from the wave buffer: a literal run row by row; a mixed
+// input's literals are first scattered into its tile at their subtile words
+// (position bytes), then read back row by row (the tile is left zero again),
+// and its ones-fill words come from the ones mask.
 __device__ __forceinline__ void staged_decode(const unsigned char* base, const uint32_t* dir,
-                                              uint32_t r0, uint32_t rend, uint32_t x0,
-                                              uint32_t x1, uint32_t lane,
+                                              StageWarp& sw, uint32_t r0, uint32_t rend,
+                                              uint32_t x0, uint32_t x1, uint32_t lane,
                                               uint64_t (&v)[kGroup][kRows]) {
-    const uint32_t bit = 1u << lane;
-    const uint32_t lt = bit - 1u;
+    uint32_t e[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) {
+        e[j] = r0 + j < rend ? dir[r0 + j] : 0u;
+        if (!((e[j] >> 13) & 1u)) continue;  // not mixed (or absent)
+        const uint32_t len = e[j] >> 19, off = e[j] & 0xFFFu;
+        const uint64_t* data = reinterpret_cast<const uint64_t*>(base + off) + ((e[j] >> 12) & 1u);
+        const unsigned char* pos = base + off + data_bytes(len, (e[j] >> 12) & 1u) +
+                                   ((e[j] >> 15) & 15u);
+#pragma unroll
+        for (uint32_t t = 0; t < uint32_t(kGW); t += 32) {
+            if (t >= len) break;
+            const uint32_t k = t + lane;
+            if (k < len) {
+                const uint32_t at = pos[k];
+                if (at < uint32_t(kGW)) sw.tile[j][at] = data[k];
+            }
+        }
+    }
+    __syncwarp();
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) v[j][r] = 0;
         if (r0 + j >= rend) continue;
-        const uint32_t ej = dir[r0 + j];
-        const unsigned char* at = base + (ej & 0xFFFu);
-        const uint64_t* data = reinterpret_cast<const uint64_t*>(at) + ((ej >> 12) & 1u);
-        if (!((ej >> 13) & 1u)) {  // a literal run: the subtile's words in order
+        const unsigned char* at = base + (e[j] & 0xFFFu);
+        if (!((e[j] >> 13) & 1u)) {  // a literal run: the subtile's words in order
+            const uint64_t* data = reinterpret_cast<const uint64_t*>(at) + ((e[j] >> 12) & 1u);
 #pragma unroll
             for (int r = 0; r < kRows; ++r)
                 if (x0 + 32 * r + lane < x1) v[j][r] = data[32 * r + lane];
             continue;
         }
-        const MaskRec* m = reinterpret_cast<const MaskRec*>(at - sizeof(MaskRec));
-        const uint4 lmv = *reinterpret_cast<const uint4*>(m->lm);
-        const uint4 cmv = *reinterpret_cast<const uint4*>(m->cm);
-        const uint32_t pre = m->pre;
-        const uint32_t lm[4] = {lmv.x, lmv.y, lmv.z, lmv.w};
-        const uint32_t cm[4] = {cmv.x, cmv.y, cmv.z, cmv.w};
-        if ((ej >> 14) & 1u) {  // ones-fill words too
-            const uint4 omv = *reinterpret_cast<const uint4*>(m->om);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            v[j][r] = sw.tile[j][32 * r + lane];
+            sw.tile[j][32 * r + lane] = 0ull;
+        }
+        if ((e[j] >> 14) & 1u) {  // ones-fill words
+            const uint4 omv = *reinterpret_cast<const uint4*>(at - 16);
             const uint32_t om[4] = {omv.x, omv.y, omv.z, omv.w};
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                if ((lm[r] | om[r]) == 0u) continue;
-                const uint32_t off = ((pre >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
-                v[j][r] = (lm[r] & bit) ? data[off] : ((om[r] & bit) ? ~0ull : 0ull);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                if (lm[r] == 0u) continue;
-                const uint32_t off = ((pre >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
-                if (lm[r] & bit) v[j][r] = data[off];
-            }
+            for (int r = 0; r < kRows; ++r)
+                if ((om[r] >> lane) & 1u) v[j][r] = ~0ull;
         }
     }
+    __syncwarp();
 }
 
 // The largest number of inputs with a non-zero word at one position of the
@@ -301,9 +322,10 @@ __device__ __forceinline__ uint32_t staged_max_position_count(const PassAParams&
 // records; decide the subtile by run-aware pruning (Sec. 6.4 cases 1 and 2,
 // and the finer position bound) when it can.  `prev` carries the item's
 // values from chunk to chunk.
-__device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, const QView& q,
-                                          uint32_t it, uint32_t c0, const Unit& prev,
-                                          uint32_t par, uint32_t& loaded, uint32_t lane) {
+__device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, StageWarp& sw,
+                                          const QView& q, uint32_t it, uint32_t c0,
+                                          const Unit& prev, uint32_t par, uint32_t& loaded,
+                                          uint32_t lane) {
     Unit u = prev;
     u.it = it;
     u.c0 = c0;
@@ -387,6 +409,19 @@ __device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, co
     }
     __syncwarp();
     u.nrec = nrec;
+    uint32_t acc = 0;  // bytes prefix of the records (the waves' cut points)
+    for (uint32_t j0 = 0; j0 < nrec; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t incl = j < nrec ? record_bytes(ws.rec[j]) : 0u;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint32_t t = __shfl_up_sync(~0u, incl, dd);
+            if (lane >= uint32_t(dd)) incl += t;
+        }
+        if (j < nrec) sw.psum[j] = acc + incl;
+        acc += __shfl_sync(~0u, incl, 31);
+    }
+    __syncwarp();
     if (one_chunk) {
         u.k = k1;
         u.d = nrec;
@@ -407,11 +442,12 @@ __device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, co
 // Add the records [wbeg, wend) of a wave in buffer `base` to the counters.
 template <class Count>
 __device__ __forceinline__ void add_wave(const unsigned char* base, const uint32_t* dir,
-                                         uint32_t wbeg, uint32_t wend, uint32_t zmode,
-                                         uint32_t x0, uint32_t x1, uint32_t lane, Count& count) {
+                                         StageWarp& sw, uint32_t wbeg, uint32_t wend,
+                                         uint32_t zmode, uint32_t x0, uint32_t x1,
+                                         uint32_t lane, Count& count) {
     for (uint32_t r0 = wbeg; r0 < wend; r0 += kGroup) {
         uint64_t v[kGroup][kRows];
-        staged_decode(base, dir, r0, wend, x0, x1, lane, v);
+        staged_decode(base, dir, sw, r0, wend, x0, x1, lane, v);
         if (zmode) {  // count the zeros of the active inputs
 #pragma unroll
             for (int j = 0; j < kGroup; ++j)
@@ -463,6 +499,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
         mbar_init(smem_addr(&sw.bar[1]), 1);
         fence_mbar_init();
     }
+    for (uint32_t i = lane; i < uint32_t(kGroup * kGW); i += 32) (&sw.tile[0][0])[i] = 0ull;
     __syncwarp();
     const QView q{ws, p.ids};
     const uint32_t nwarps = gridDim.x * kNW;
@@ -479,7 +516,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
     uint32_t phase = 0;     // per buffer: parity of its next completion
     uint32_t waves = 0;     // records of the wave in each buffer
     Unit cur{};
-    cur = plan_unit(p, ws, q, first, 0, cur, 0u, loaded, lane);
+    cur = plan_unit(p, ws, sw, q, first, 0, cur, 0u, loaded, lane);
     uint32_t b = 0;  // the buffer of cur's next wave
     if (cur.flags & kUCount) issue_wave(p, ws, sw, cur, b, lane, waves);
     while (cur.it < nitems) {
@@ -497,9 +534,9 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
                     issue_wave(p, ws, sw, cur, b ^ 1u, lane, waves);
                 } else {  // the next unit, and its first wave
                     nxt = (cur.flags & kULast)
-                              ? plan_unit(p, ws, q, next_item(cur.it), 0, cur, par ^ 1u, loaded,
+                              ? plan_unit(p, ws, sw, q, next_item(cur.it), 0, cur, par ^ 1u, loaded,
                                           lane)
-                              : plan_unit(p, ws, q, cur.it, cur.c0 + kCH, cur, par ^ 1u,
+                              : plan_unit(p, ws, sw, q, cur.it, cur.c0 + kCH, cur, par ^ 1u,
                                           loaded, lane);
                     planned = true;
                     if (nxt.flags & kUCount)
@@ -513,7 +550,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
                     return;
                 }
                 phase ^= 1u << b;
-                add_wave(sw.buf[b], sw.dir[par], wave_begin(waves, b), wave_end(waves, b),
+                add_wave(sw.buf[b], sw.dir[par], sw, wave_begin(waves, b), wave_end(waves, b),
                          (cur.flags >> 4) & 1u, x0, x1, lane, count);
                 __syncwarp();
                 b ^= 1u;
@@ -523,8 +560,8 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
         if (cur.flags & kULast) finish_unit(p, ws, cur, lane, count);
         if (!planned) {  // nothing was counted: plan the next unit now
             nxt = (cur.flags & kULast)
-                      ? plan_unit(p, ws, q, next_item(cur.it), 0, cur, par ^ 1u, loaded, lane)
-                      : plan_unit(p, ws, q, cur.it, cur.c0 + kCH, cur, par ^ 1u, loaded, lane);
+                      ? plan_unit(p, ws, sw, q, next_item(cur.it), 0, cur, par ^ 1u, loaded, lane)
+                      : plan_unit(p, ws, sw, q, cur.it, cur.c0 + kCH, cur, par ^ 1u, loaded, lane);
             if (nxt.flags & kUCount) issue_wave(p, ws, sw, nxt, b, lane, waves);
         }
         cur = nxt;
@@ -533,7 +570,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
 
 // The staged carry-save kernel, S-bit counters.
 template <int S>
-__global__ void __launch_bounds__(kNT, (S <= 4 ? 4 : (S <= 8 ? 3 : 2))) k_staged(const PassAParams p) {
+__global__ void __launch_bounds__(kNT, (S <= 8 ? 3 : 2)) k_staged(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StagedCta& sm = *reinterpret_cast<StagedCta*>(smem_raw);
     CsaCount<S> count;
