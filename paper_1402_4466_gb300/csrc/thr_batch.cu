@@ -454,7 +454,6 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                             static_cast<const void*>(idx->d_pcls),
                             static_cast<const void*>(idx->d_masks),
                             static_cast<const void*>(idx->d_sseg),
-                            static_cast<const void*>(idx->d_spos),
                             static_cast<const void*>(idx->d_desc)})
         sig = fnv(sig, reinterpret_cast<uintptr_t>(ptr));
     sig = fnv(sig, uint64_t(idx->W) << 32 | idx->NG);

@@ -251,38 +251,6 @@ __global__ void k_subtile_masks(const uint2* __restrict__ mtab,
     sseg[i] = uint64_t(base) | (uint64_t(run) << 32);
 }
 
-// Position bytes (spos): for every stream word, the word of its subtile it
-// is (0 .. 127) when it is a literal, 0xFF when it is a marker.  One CTA per
-// bitmap; a thread finds the marker group of its stream word by binary search
-// over the bitmap's marker positions (mtab): the k-th literal of a group
-// whose literals end at uncompressed word ue sits at ue - L + k.
-__global__ void k_stream_pos(const uint2* __restrict__ mtab, const BitmapDesc* __restrict__ desc,
-                             uint8_t* __restrict__ spos) {
-    const BitmapDesc d = desc[blockIdx.x];
-    const uint2* mt = mtab + d.moff;
-    for (uint32_t j = threadIdx.x; j < d.len; j += blockDim.x) {
-        uint32_t lo = 0, hi = d.nmark;  // mt[lo].x <= j < mt[hi].x
-        while (hi - lo > 1) {
-            const uint32_t mid = lo + (hi - lo) / 2;
-            if (mt[mid].x <= j) lo = mid;
-            else hi = mid;
-        }
-        uint8_t v = 0xFF;
-        if (mt[lo].x != j) {
-            const uint32_t L = mt[lo + 1].x - mt[lo].x - 1;
-            const uint32_t ue = mt[lo + 1].y & 0x7fffffffu;
-            v = uint8_t((ue - L + (j - mt[lo].x - 1)) & uint32_t(kGW - 1));
-        }
-        spos[d.woff + j] = v;
-    }
-}
-
-cudaError_t launch_stream_pos(const uint2* mtab, const BitmapDesc* desc, uint8_t* spos,
-                              uint32_t nbitmaps, cudaStream_t st) {
-    k_stream_pos<<<nbitmaps, 256, 0, st>>>(mtab, desc, spos);
-    return cudaGetLastError();
-}
-
 // Thread per (bitmap, word): the classes of 32 consecutive subtiles.
 __global__ void k_pack_classes(const uint64_t* __restrict__ sdesc, uint64_t* __restrict__ pcls,
                                uint32_t nbitmaps, uint32_t NG, uint32_t NGW) {

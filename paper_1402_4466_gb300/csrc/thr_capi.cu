@@ -381,7 +381,6 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         (e = cudaMalloc(&idx->d_mtab, sizeof(uint2) * moff)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_sdesc, sizeof(uint64_t) * sdesc_n)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_sseg, sizeof(uint64_t) * sdesc_n)) != cudaSuccess ||
-        (e = cudaMalloc(&idx->d_spos, total + 32)) != cudaSuccess ||
         (e = cudaMalloc(&idx->d_desc, sizeof(BitmapDesc) * nbitmaps)) != cudaSuccess ||
         (e = cudaMalloc(&d_ttab, sizeof(uint32_t) * ttab_n)) != cudaSuccess ||
         (e = cudaMalloc(&d_mpos, sizeof(uint32_t) * std::max<uint64_t>(mpos.size(), 1))) != cudaSuccess) {
@@ -389,7 +388,6 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
         return cleanup(cuda_fail(e, "index allocation"));
     }
     if ((e = cudaMemsetAsync(idx->d_words + total, 0, 2 * sizeof(uint64_t), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(idx->d_spos + total, 0xFF, 32, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(idx->d_words, words, sizeof(uint64_t) * total,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_mpos, mpos.data(), sizeof(uint32_t) * mpos.size(),
@@ -438,7 +436,6 @@ thr_status idx_build_rle(const uint64_t* words, const uint64_t* offsets,
     if (e == cudaSuccess)
         e = cudaMalloc(&idx->d_pcls, sizeof(uint64_t) * uint64_t(nbitmaps) * ((idx->NG + 31) / 32));
     if (e == cudaSuccess) e = launch_pack_classes(idx->d_sdesc, idx->d_pcls, nbitmaps, idx->NG, st);
-    if (e == cudaSuccess) e = launch_stream_pos(idx->d_mtab, idx->d_desc, idx->d_spos, nbitmaps, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     free_all_tmp();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "index build kernels"));
@@ -458,7 +455,6 @@ void idx_free(thr_index* idx) {
     cudaFree(idx->d_pcls);
     cudaFree(idx->d_masks);
     cudaFree(idx->d_sseg);
-    cudaFree(idx->d_spos);
     cudaFree(idx->d_desc);
     cudaSetDevice(cur);
     delete idx;

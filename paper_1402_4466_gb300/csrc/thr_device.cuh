@@ -22,8 +22,6 @@
 //          (a literal run: its literals; mixed: the literals and the markers
 //          between them, from MaskRec::base on; else 0).  The staged kernel
 //          copies exactly these words to shared memory.
-//   spos   one byte per stream word: the word of its 128-word subtile a
-//          literal is (0 .. 127), 0xFF for a marker word.
 //
 // A query (or a batch of them) runs in three passes:
 //   A  k_threshold<S> / k_scancount: persistent grid; a warp takes a work
@@ -121,7 +119,6 @@ struct PassAParams {
     const uint64_t* pcls;   // packed subtile classes, NGW words per bitmap
     const MaskRec* masks;   // mask records of the mixed subtiles
     const uint64_t* sseg;   // segment descriptors, NG per bitmap
-    const uint8_t* spos;    // position byte of every stream word
     uint32_t* err;          // set to a non-zero code when a kernel gave up waiting
     uint32_t lose;          // test hook: each staged slot expects 16 bytes more than
                             // it is sent, so its wait runs out (THR_TEST_LOST_COPY)
@@ -360,9 +357,6 @@ cudaError_t launch_index_build_a(const uint64_t* words, const uint32_t* mpos,
                                  uint64_t* sdesc, uint64_t* sseg, uint32_t* mixed_count,
                                  uint32_t nbitmaps, uint32_t W, uint32_t NG,
                                  cudaStream_t st);
-// Position bytes of every stream word (spos, see k_stream_pos).
-cudaError_t launch_stream_pos(const uint2* mtab, const BitmapDesc* desc, uint8_t* spos,
-                              uint32_t nbitmaps, cudaStream_t st);
 // Packed classes from the final subtile descriptors (after part b).
 cudaError_t launch_pack_classes(const uint64_t* sdesc, uint64_t* pcls, uint32_t nbitmaps,
                                 uint32_t NG, cudaStream_t st);

@@ -173,7 +173,6 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     p.NGW = (NG + 31) / 32;
     p.masks = idx->d_masks;
     p.sseg = idx->d_sseg;
-    p.spos = idx->d_spos;
     p.err = reinterpret_cast<uint32_t*>(s + l.err);
     p.lose = test_lost_copy();
     p.desc = idx->d_desc;

@@ -28,7 +28,6 @@ struct thr_index {
     uint64_t* d_pcls = nullptr;   // their classes, 2 bits each, ceil(NG/32) words per bitmap
     thr::MaskRec* d_masks = nullptr;  // mask records of the mixed subtiles
     uint64_t* d_sseg = nullptr;   // NG segment descriptors per bitmap
-    uint8_t* d_spos = nullptr;    // total_words + 32 position bytes (pad for 16-byte copies)
     uint64_t mixed_subtiles = 0;
     thr::BitmapDesc* d_desc = nullptr;
     std::vector<thr::BitmapDesc> desc;

@@ -131,7 +131,6 @@ thr_status profile_pass(const thr_index* idx, uint32_t nq, const uint32_t* id_of
     p.pcls = idx->d_pcls;
     p.masks = idx->d_masks;
     p.sseg = idx->d_sseg;
-    p.spos = idx->d_spos;
     p.desc = idx->d_desc;
     p.qd = reinterpret_cast<const QDesc*>(d);
     p.ids = reinterpret_cast<const uint32_t*>(d + o_ids);

@@ -1,23 +1,30 @@
-// Pass A with staged inputs (k_staged<S>, THR_VARIANT_STAGED): carry-save counting fed by bulk copies.
+// Pass A with staged inputs (k_staged<S>, THR_VARIANT_STAGED).
 //
 // The counting and the re-encoding are those of k_threshold<S>
 // (thr_query_kernel.cuh); what changes is how an input's words reach the
 // warp.  The direct kernel loads every literal word from global memory at
 // the moment it is added, after a chain of dependent loads (packed class ->
-// descriptor -> mask record -> literal), so a warp has about one group of
-// inputs in flight and waits on memory most of the time.  Here the active
-// inputs of a subtile are first classified (packed class, then the segment
-// descriptor sseg and, for a mixed input, its descriptor), and their
-// compressed words for the subtile -- one contiguous stream segment per
-// input, found at build time -- and mask records are copied into shared
-// memory by 1-D bulk copies (cp.async.bulk, completion counted in bytes on
-// an mbarrier).  Copies go in waves: a wave is as many of the chunk's inputs
-// as fit one kWaveBytes buffer; each warp has two buffers, and while it adds
-// the inputs of one wave the next wave -- the rest of the chunk, or the first
-// wave of its next work item, classified first -- is already on its way.
-// Every word of a segment is read from HBM once, in whole 16-byte units; the
+// descriptor -> mask record -> literal).  Here the active inputs of a
+// subtile are first classified (packed class, then the segment descriptor
+// sseg and, for a mixed input, its descriptor), and their compressed words
+// for the subtile -- one contiguous stream segment per input, found at build
+// time -- and mask records are copied into shared memory by 1-D bulk copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier).  Copies go in
+// waves: a wave is as many of the chunk's inputs as fit one kWaveBytes
+// buffer (the cut points come from a prefix of the records' sizes computed
+// once per chunk); each warp has two buffers, and while it adds the inputs
+// of one wave the next wave -- the rest of the chunk, or the first wave of
+// its next work item, classified first -- is already on its way.  Every
+// word of a segment is read from HBM once, in whole 16-byte units; the
 // decode then finds a mixed input's literal at segment word pre[r] +
 // popc(cm[r] below the lane) in shared memory.
+//
+// Measured on the 64 x 2^26 many-criteria bitmaps at T = 2 it is slower than
+// the direct kernel (94 vs 75 us): the memory latency is hidden, but one
+// bulk copy per input and subtile (about 640 thousand per query, ~300 bytes
+// on average) with a wait per wave costs 52 us on its own, without any
+// decode or add.  It stays as a variant for queries whose inputs are long
+// literal runs.
 //
 // A copy starts at an even stream word (16 bytes) and covers whole 16-byte
 // units, so it may read one word before the segment and one after it; the
@@ -31,7 +38,7 @@
 
 namespace thr {
 
-constexpr int kWaveBytes = 4096;  // one wave buffer
+constexpr int kWaveBytes = 3840;  // one wave buffer
 // the largest input: a mask record and kGW words from an odd stream word,
 // in 16-byte units
 static_assert(sizeof(MaskRec) + 16 * ((8 * (kGW + 1) + 15) / 16) <= kWaveBytes,
@@ -40,13 +47,9 @@ static_assert(kWaveBytes <= (1 << 12), "wave offsets take 12 bits");
 
 struct StageWarp {
     alignas(16) unsigned char buf[2][kWaveBytes];
-    // a mixed input's literals are scattered into its tile (one per input of
-    // a group of kGroup) at their subtile words, then read back row by row
-    unsigned long long tile[kGroup][kGW];
     unsigned long long bar[2];  // one mbarrier per buffer
     // [unit parity][record]: byte offset of the record's words in its wave's
     // buffer | first word odd << 12 | mixed << 13 | has ones-fill words << 14
-    // | first position byte's offset in its 16-byte unit << 15 | words << 19
     uint32_t dir[2][kCH];
     uint32_t psum[kCH];  // bytes the unit's records take in waves, inclusive prefix
 };
@@ -151,20 +154,14 @@ __device__ __forceinline__ uint32_t wave_end(uint32_t w, uint32_t b) {
     return (w >> (16 * b + 8)) & 0xFFu;
 }
 
-// Bytes a record takes in a wave, in 16-byte units: a literal run its
-// words; a mixed input its words, their position bytes and, with ones-fill
-// words, the 16-byte ones mask of its mask record.
+// Bytes a record takes in a wave, in 16-byte units: its words, and for a
+// mixed input its 64-byte mask record in front of them.
 __device__ __forceinline__ uint32_t data_bytes(uint32_t len, uint32_t odd) {
     return (8u * (len + odd) + 15u) & ~15u;
 }
-__device__ __forceinline__ uint32_t pos_bytes(uint32_t len, uint32_t mis) {
-    return (mis + len + 15u) & ~15u;
-}
 __device__ __forceinline__ uint32_t record_bytes(const uint4& rec) {
     const uint32_t len = (rec.y >> 8) & 0x1FFu;
-    uint32_t b = data_bytes(len, rec.x & 1u);
-    if (rec.y >> 31) b += pos_bytes(len, rec.x & 15u) + (((rec.y >> 30) & 1u) ? 16u : 0u);
-    return b;
+    return data_bytes(len, rec.x & 1u) + ((rec.y >> 31) ? uint32_t(sizeof(MaskRec)) : 0u);
 }
 
 // Send the unit's next records, as many as fit buffer b, as one wave: the
@@ -197,21 +194,14 @@ __device__ __forceinline__ void issue_wave(const PassAParams& p, const WarpCore&
         const uint64_t seg = (uint64_t(rec.y & 0xFFu) << 32) | rec.x;
         const uint32_t len = (rec.y >> 8) & 0x1FFu;
         const uint32_t odd = rec.x & 1u, mixed = rec.y >> 31, ones = (rec.y >> 30) & 1u;
-        const uint32_t mis = rec.x & 15u;
         uint32_t off = sw.psum[j] - start - record_bytes(rec);
-        if (ones) {  // the ones mask: bytes 32 .. 47 of the mask record
-            bulk_copy(smem_addr(base + off),
-                      reinterpret_cast<const unsigned char*>(
-                          p.masks + ((uint64_t(rec.w) << 32) | rec.z)) + 32,
-                      16u, bar);
-            off += 16u;
+        if (mixed) {
+            bulk_copy(smem_addr(base + off), p.masks + ((uint64_t(rec.w) << 32) | rec.z),
+                      uint32_t(sizeof(MaskRec)), bar);
+            off += uint32_t(sizeof(MaskRec));
         }
-        const uint32_t db = data_bytes(len, odd);
-        bulk_copy(smem_addr(base + off), p.words + (seg & ~1ull), db, bar);
-        if (mixed)
-            bulk_copy(smem_addr(base + off + db), p.spos + (seg & ~15ull), pos_bytes(len, mis),
-                      bar);
-        dir[j] = off | (odd << 12) | (mixed << 13) | (ones << 14) | (mis << 15) | (len << 19);
+        bulk_copy(smem_addr(base + off), p.words + (seg & ~1ull), data_bytes(len, odd), bar);
+        dir[j] = off | (odd << 12) | (mixed << 13) | (ones << 14);
     }
     __syncwarp();
     waves = (waves & ~(0xFFFFu << (16 * b))) | ((r0 | (r << 8)) << (16 * b));
@@ -219,61 +209,53 @@ __device__ __forceinline__ void issue_wave(const PassAParams& p, const WarpCore&
 }
 
 // Values of records r0 .. r0 + kGroup - 1 (< rend) at the lane's words
-// x0 + 32 r + lane, from the wave buffer: a literal run row by row; a mixed
-// input's literals are first scattered into its tile at their subtile words
-// (position bytes), then read back row by row (the tile is left zero again),
-// and its ones-fill words come from the ones mask.
+// x0 + 32 r + lane, from the wave buffer: a literal run row by row, a mixed
+// input through its mask record (the literal at segment word pre[r] +
+// popc(cm[r] below the lane); a ones-fill word from the ones mask; else 0).
 __device__ __forceinline__ void staged_decode(const unsigned char* base, const uint32_t* dir,
-                                              StageWarp& sw, uint32_t r0, uint32_t rend,
-                                              uint32_t x0, uint32_t x1, uint32_t lane,
+                                              uint32_t r0, uint32_t rend, uint32_t x0,
+                                              uint32_t x1, uint32_t lane,
                                               uint64_t (&v)[kGroup][kRows]) {
-    uint32_t e[kGroup];
-#pragma unroll
-    for (int j = 0; j < kGroup; ++j) {
-        e[j] = r0 + j < rend ? dir[r0 + j] : 0u;
-        if (!((e[j] >> 13) & 1u)) continue;  // not mixed (or absent)
-        const uint32_t len = e[j] >> 19, off = e[j] & 0xFFFu;
-        const uint64_t* data = reinterpret_cast<const uint64_t*>(base + off) + ((e[j] >> 12) & 1u);
-        const unsigned char* pos = base + off + data_bytes(len, (e[j] >> 12) & 1u) +
-                                   ((e[j] >> 15) & 15u);
-#pragma unroll
-        for (uint32_t t = 0; t < uint32_t(kGW); t += 32) {
-            if (t >= len) break;
-            const uint32_t k = t + lane;
-            if (k < len) {
-                const uint32_t at = pos[k];
-                if (at < uint32_t(kGW)) sw.tile[j][at] = data[k];
-            }
-        }
-    }
-    __syncwarp();
+    const uint32_t bit = 1u << lane;
+    const uint32_t lt = bit - 1u;
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) {
 #pragma unroll
         for (int r = 0; r < kRows; ++r) v[j][r] = 0;
         if (r0 + j >= rend) continue;
-        const unsigned char* at = base + (e[j] & 0xFFFu);
-        if (!((e[j] >> 13) & 1u)) {  // a literal run: the subtile's words in order
-            const uint64_t* data = reinterpret_cast<const uint64_t*>(at) + ((e[j] >> 12) & 1u);
+        const uint32_t ej = dir[r0 + j];
+        const unsigned char* at = base + (ej & 0xFFFu);
+        const uint64_t* data = reinterpret_cast<const uint64_t*>(at) + ((ej >> 12) & 1u);
+        if (!((ej >> 13) & 1u)) {  // a literal run: the subtile's words in order
 #pragma unroll
             for (int r = 0; r < kRows; ++r)
                 if (x0 + 32 * r + lane < x1) v[j][r] = data[32 * r + lane];
             continue;
         }
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            v[j][r] = sw.tile[j][32 * r + lane];
-            sw.tile[j][32 * r + lane] = 0ull;
-        }
-        if ((e[j] >> 14) & 1u) {  // ones-fill words
-            const uint4 omv = *reinterpret_cast<const uint4*>(at - 16);
+        const MaskRec* m = reinterpret_cast<const MaskRec*>(at - sizeof(MaskRec));
+        const uint4 lmv = *reinterpret_cast<const uint4*>(m->lm);
+        const uint4 cmv = *reinterpret_cast<const uint4*>(m->cm);
+        const uint32_t pre = m->pre;
+        const uint32_t lm[4] = {lmv.x, lmv.y, lmv.z, lmv.w};
+        const uint32_t cm[4] = {cmv.x, cmv.y, cmv.z, cmv.w};
+        if ((ej >> 14) & 1u) {  // ones-fill words too
+            const uint4 omv = *reinterpret_cast<const uint4*>(m->om);
             const uint32_t om[4] = {omv.x, omv.y, omv.z, omv.w};
 #pragma unroll
-            for (int r = 0; r < kRows; ++r)
-                if ((om[r] >> lane) & 1u) v[j][r] = ~0ull;
+            for (int r = 0; r < kRows; ++r) {
+                if ((lm[r] | om[r]) == 0u) continue;
+                const uint32_t off = ((pre >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
+                v[j][r] = (lm[r] & bit) ? data[off] : ((om[r] & bit) ? ~0ull : 0ull);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                if (lm[r] == 0u) continue;
+                const uint32_t off = ((pre >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
+                if (lm[r] & bit) v[j][r] = data[off];
+            }
         }
     }
-    __syncwarp();
 }
 
 // The largest number of inputs with a non-zero word at one position of the
@@ -442,12 +424,11 @@ __device__ __forceinline__ Unit plan_unit(const PassAParams& p, WarpCore& ws, St
 // Add the records [wbeg, wend) of a wave in buffer `base` to the counters.
 template <class Count>
 __device__ __forceinline__ void add_wave(const unsigned char* base, const uint32_t* dir,
-                                         StageWarp& sw, uint32_t wbeg, uint32_t wend,
-                                         uint32_t zmode, uint32_t x0, uint32_t x1,
-                                         uint32_t lane, Count& count) {
+                                         uint32_t wbeg, uint32_t wend, uint32_t zmode,
+                                         uint32_t x0, uint32_t x1, uint32_t lane, Count& count) {
     for (uint32_t r0 = wbeg; r0 < wend; r0 += kGroup) {
         uint64_t v[kGroup][kRows];
-        staged_decode(base, dir, sw, r0, wend, x0, x1, lane, v);
+        staged_decode(base, dir, r0, wend, x0, x1, lane, v);
         if (zmode) {  // count the zeros of the active inputs
 #pragma unroll
             for (int j = 0; j < kGroup; ++j)
@@ -499,7 +480,6 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
         mbar_init(smem_addr(&sw.bar[1]), 1);
         fence_mbar_init();
     }
-    for (uint32_t i = lane; i < uint32_t(kGroup * kGW); i += 32) (&sw.tile[0][0])[i] = 0ull;
     __syncwarp();
     const QView q{ws, p.ids};
     const uint32_t nwarps = gridDim.x * kNW;
@@ -550,7 +530,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
                     return;
                 }
                 phase ^= 1u << b;
-                add_wave(sw.buf[b], sw.dir[par], sw, wave_begin(waves, b), wave_end(waves, b),
+                add_wave(sw.buf[b], sw.dir[par], wave_begin(waves, b), wave_end(waves, b),
                          (cur.flags >> 4) & 1u, x0, x1, lane, count);
                 __syncwarp();
                 b ^= 1u;
@@ -570,7 +550,7 @@ __device__ __forceinline__ void staged_pass_a(const PassAParams& p, StagedCta& s
 
 // The staged carry-save kernel, S-bit counters.
 template <int S>
-__global__ void __launch_bounds__(kNT, (S <= 8 ? 3 : 2)) k_staged(const PassAParams p) {
+__global__ void __launch_bounds__(kNT, (S <= 4 ? 4 : (S <= 8 ? 3 : 2))) k_staged(const PassAParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StagedCta& sm = *reinterpret_cast<StagedCta*>(smem_raw);
     CsaCount<S> count;
