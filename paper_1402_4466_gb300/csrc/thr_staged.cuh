@@ -23,8 +23,8 @@
 // the direct kernel (94 vs 75 us): the memory latency is hidden, but one
 // bulk copy per input and subtile (about 640 thousand per query, ~300 bytes
 // on average) with a wait per wave costs 52 us on its own, without any
-// decode or add.  It stays as a variant for queries whose inputs are long
-// literal runs.
+// decode or add.  It is a flag-selected variant, not an arm of the
+// policies.
 //
 // A copy starts at an even stream word (16 bytes) and covers whole 16-byte
 // units, so it may read one word before the segment and one after it; the
