@@ -88,9 +88,11 @@ typedef enum {
  *                          decoded position by position (each lane walks the
  *                          inputs with a literal at its word), so their cost
  *                          follows their literals: for sparse inputs
- *   THR_VARIANT_SCANCOUNT  ScanCount: one byte counter per row in shared
- *                          memory per subtile (Sec. 5.1), for very sparse
- *                          inputs; used when n <= 255, else CSA runs
+ *   THR_VARIANT_SCANCOUNT  ScanCount: one counter per row in shared memory
+ *                          per subtile (Sec. 5.1), bytes for n <= 255 and
+ *                          16 bits for n <= 65535 (else CSA runs); only the
+ *                          bit positions some input set are compared, so the
+ *                          cost follows the set bits: for very sparse inputs
  *   THR_VARIANT_SPLIT      THR_VARIANT_CSA with each subtile's inputs split
  *                          among the four warps of a CTA, whose counters are
  *                          then added: more parallelism for queries with

@@ -294,7 +294,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         // the chunk's shape and its launch configuration
         uint64_t present = 0;
         double sum_n = 0;
-        int widest[kNumFamilies] = {-1, -1, -1, -1, -1};  // per family
+        int widest[kNumFamilies];  // per family
+        std::fill(widest, widest + kNumFamilies, -1);
         for (uint32_t s = 0; s < Q; ++s) {
             if (absorbed[q0 + s]) continue;
             const int c = qcls[q0 + s];
@@ -320,7 +321,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
             if (absorbed[q0 + s]) continue;
             const int c = qcls[q0 + s];
             const double w =
-                double(qd[q0 + s].n) * (c == kClassScanCount ? 4.0 : 2.0 + class_width(c));
+                double(qd[q0 + s].n) * (class_family(c) == 1 ? 4.0 : 2.0 + class_width(c));
             work[c] += w;
             work_all += w;
         }

@@ -30,7 +30,7 @@ int slices_for(uint64_t t) { return t <= 2 ? 1 : bits_of(t - 1); }
 namespace {
 
 cudaError_t launch_class(int cls, const PassAParams& p, int grid, cudaStream_t st) {
-    if (cls == kClassScanCount) return launch_scancount(p, grid, st);
+    if (class_family(cls) == 1) return launch_scancount(cls == kClassScanCount16, p, grid, st);
     if (class_family(cls) == 4)
         return cls < kNumClasses ? launch_looped(cls - kClassLooped + 1, p, grid, st)
                                  : cudaErrorInvalidValue;
@@ -108,8 +108,8 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
         *zmode = 0;
         return;
     }
-    if (v == kVarScanCount && n <= 255) {
-        *cls = kClassScanCount;
+    if (v == kVarScanCount && n <= 65535) {
+        *cls = n <= 255 ? kClassScanCount : kClassScanCount16;
         *zmode = 0;
         return;
     }
@@ -138,7 +138,7 @@ void resolve_variant(uint32_t n, uint32_t T, int v, int* cls, uint32_t* zmode) {
 }
 
 cudaError_t class_occupancy(int cls, int* per_sm) {
-    if (cls == kClassScanCount) return occupancy_scancount(per_sm);
+    if (class_family(cls) == 1) return occupancy_scancount(cls == kClassScanCount16, per_sm);
     if (class_family(cls) == 4)
         return cls < kNumClasses ? occupancy_looped(cls - kClassLooped + 1, per_sm)
                                  : cudaErrorInvalidValue;

@@ -15,7 +15,7 @@ namespace thr {
 
 // Kernel classes: 0 .. kNumWidths-1 carry-save with the counter width
 // kernel_table()[c].S (grouped decode), kClassScanCount the
-// ScanCount kernel, kClassPos + c carry-save of width kernel_table()[c].S
+// ScanCount kernel with byte counters (kClassScanCount + 1: 16-bit counters), kClassPos + c carry-save of width kernel_table()[c].S
 // with the position-major decode of mixed inputs, kClassSplit + c carry-save
 // with the inputs split among the CTA's warps (widths up to kSplitWidths),
 // kClassLooped + M - 1 Looped with M levels (M = 1 .. kLoopedMax),
@@ -25,8 +25,9 @@ constexpr int kNumWidths = 12;
 constexpr int kSplitWidths = 8;  // S = 1..8
 constexpr int kLoopedMax = 4;    // Looped levels (thresholds) instantiated
 constexpr int kClassScanCount = kNumWidths;
-constexpr int kClassPos = kNumWidths + 1;
-constexpr int kClassSplit = 2 * kNumWidths + 1;
+constexpr int kClassScanCount16 = kNumWidths + 1;
+constexpr int kClassPos = kNumWidths + 2;
+constexpr int kClassSplit = 2 * kNumWidths + 2;
 constexpr int kClassLooped = kClassSplit + kSplitWidths;
 constexpr int kClassStaged = kClassLooped + kLoopedMax;
 constexpr int kNumClasses = kClassStaged + kNumWidths;
@@ -37,7 +38,7 @@ constexpr int kNumFamilies = 6;
 inline int class_family(int c) {
     return c < kNumWidths
                ? 0
-               : (c == kClassScanCount
+               : (c <= kClassScanCount16
                       ? 1
                       : (c < kClassSplit ? 2
                                          : (c < kClassLooped ? 3 : (c < kClassStaged ? 4 : 5))));
@@ -46,11 +47,13 @@ inline int class_family(int c) {
 inline int class_width(int c) {
     return c < kNumWidths
                ? c
-               : (c < kClassSplit
-                      ? c - kClassPos
-                      : (c < kClassLooped ? c - kClassSplit
-                                          : (c < kClassStaged ? c - kClassLooped
-                                                              : c - kClassStaged)));
+               : (c <= kClassScanCount16
+                      ? c - kClassScanCount
+                      : (c < kClassSplit
+                             ? c - kClassPos
+                             : (c < kClassLooped ? c - kClassSplit
+                                                 : (c < kClassStaged ? c - kClassLooped
+                                                                     : c - kClassStaged))));
 }
 
 // One pass-A launch: the slots list[list_off .. list_off + nlist) of its
@@ -115,7 +118,8 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
 //                  when that needs fewer slices
 //   kVarPos        carry-save bit slices counting ones; mixed inputs decoded
 //                  position-major (cost follows their literals)
-//   kVarScanCount  ScanCount byte counters (n <= 255; else kVarCsa runs)
+//   kVarScanCount  ScanCount counters (bytes for n <= 255, 16 bits for
+//                  n <= 65535; else kVarCsa runs)
 //   kVarSplit      grouped carry-save with each subtile's inputs split among
 //                  the four warps of a CTA (S <= 8; else kVarCsa runs)
 constexpr int kVarCsa = 0, kVarPos = 1, kVarScanCount = 2, kVarSplit = 3;

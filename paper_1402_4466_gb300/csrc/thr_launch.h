@@ -23,9 +23,10 @@ struct KernelEntry {
     OccupancyFn occupancy_split;
 };
 
-// Pass A with ScanCount counters (thr_scancount.cu): n <= 255, ones only.
-cudaError_t launch_scancount(const PassAParams&, int grid, cudaStream_t);
-cudaError_t occupancy_scancount(int* blocks_per_sm);
+// Pass A with ScanCount counters (thr_scancount.cu), ones only: byte counters
+// for n <= 255, 16-bit counters (wide) for n <= 65535.
+cudaError_t launch_scancount(bool wide, const PassAParams&, int grid, cudaStream_t);
+cudaError_t occupancy_scancount(bool wide, int* blocks_per_sm);
 
 // Pass A with Looped levels (thr_inst_looped.cu), M = 1 .. kLoopedMax.
 cudaError_t launch_looped(int M, const PassAParams&, int grid, cudaStream_t);

@@ -84,7 +84,7 @@ uint8_t rule_choice(const thr_index* idx, const uint32_t* ids, uint32_t n, uint3
                          m.s0 + m.s1 * words + m.s2 * words * S};
     int best = kVarCsa;
     for (int v = 1; v < 4; ++v) {
-        if (v == kVarScanCount && n > 255) continue;
+        if (v == kVarScanCount && n > 65535) continue;
         if (v == kVarSplit && S > 8) continue;
         if (t[v] < t[best]) best = v;
     }
@@ -183,7 +183,7 @@ bool split_applies(uint32_t n, uint32_t T) {
 
 // With a cost model attached to the index: features of every query, one
 // forward pass for the batch, and per query the variant with the smallest
-// predicted time among those it can run (ScanCount needs n <= 255).
+// predicted time among those it can run (ScanCount needs n <= 65535).
 thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                           const uint32_t* ids, const uint32_t* T, std::vector<uint8_t>* var,
                           bool* used) {
@@ -226,7 +226,7 @@ thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_
         int best = kVarCsa;
         float best_y = y[kVarCsa] - margin;
         for (int v = 0; v < kSelVariants; ++v) {
-            if (v == kVarCsa || (v == kVarScanCount && n > 255)) continue;
+            if (v == kVarCsa || (v == kVarScanCount && n > 65535)) continue;
             if (v == kVarSplit && !split_applies(n, T[q])) continue;
             if (y[v] < best_y) {
                 best = v;

@@ -222,8 +222,29 @@ def test_scancount_several_tiles_and_duplicates():
     ids = rng.integers(0, 24, size=200).tolist()  # two chunks, n <= 255
     for T in (1, 2, 10, 50, 100, 200):
         p.check(ids, T, SC)
-    ids = rng.integers(0, 24, size=300).tolist()  # n > 255: the carry-save kernel runs
-    p.check(ids, 30, SC)
+    ids = rng.integers(0, 24, size=300).tolist()  # n > 255: 16-bit counters
+    for T in (1, 30, 256, 300):
+        p.check(ids, T, SC)
+    ids = rng.integers(0, 24, size=1200).tolist()  # four record chunks, 16-bit counters
+    for T in (2, 60, 700):
+        p.check(ids, T, SC)
+
+
+def test_scancount_wide_counters_sparse_and_fallback():
+    """Very sparse bitmaps (the case ScanCount is for) with more than 255
+    inputs: counts past 255 in 16-bit counters, ones fills counted per word;
+    above 65535 inputs the carry-save kernel runs instead."""
+    r = (1 << 17) + 9
+    arrays = [synth.bernoulli(33, k, r, 1e-3) for k in range(30)]
+    arrays.append(synth.rows_to_words(np.arange(1000, 9000), r))  # ones fills
+    p = Pair(arrays, r)
+    rng = np.random.default_rng(33)
+    ids = rng.integers(0, 31, size=2000).tolist() + [30] * 300
+    for T in (1, 2, 3, 250, 256, 300, 2300):
+        p.check(ids, T, SC)
+    big = rng.integers(0, 31, size=70_000).tolist()
+    for T in (2, 3000):
+        p.check(big, T, SC)
 
 
 def test_scancount_many_criteria_full_size(many_criteria_full):
