@@ -154,7 +154,10 @@ thr_status idx_build_rle(const uint64_t *words, const uint64_t *offsets,
  *   flags     THR_OUT_DEVICE or 0
  *   cuda_stream  cudaStream_t for all work (0 ok)
  * On return the result and *out_len are complete (the call synchronises
- * cuda_stream).  Concurrent queries on one index are allowed.
+ * cuda_stream).  Concurrent queries on one index are allowed.  The work is
+ * captured as a CUDA graph kept per calling thread; a later query of the
+ * same shape (input count within the same 64, variant, counter width,
+ * output buffer) on that thread replays it (not with THR_PROFILE).
  */
 thr_status thr_query(const thr_index *idx, const uint32_t *ids, uint32_t n,
                      uint32_t T, uint64_t *out, uint64_t cap,
@@ -427,9 +430,11 @@ thr_status thr_index_set_selector(thr_index *idx, const thr_selector *sel);
 
 /*
  * The counting variant (0 THR_VARIANT_CSA, 1 THR_VARIANT_POSITION,
- * 2 THR_VARIANT_SCANCOUNT, 3 THR_VARIANT_SPLIT) each query of a batch runs
- * with under the policy
- * in flags (arguments as for thr_query_batch); nothing is run.
+ * 2 THR_VARIANT_SCANCOUNT, 3 THR_VARIANT_SPLIT, 4 THR_VARIANT_LOOPED,
+ * 5 THR_VARIANT_STAGED) each query of a batch runs with under the policy in
+ * flags (arguments as for thr_query_batch), after the fallbacks (ScanCount
+ * above 65535 inputs, split above 8 counter bits and Looped above T = 4
+ * run the grouped carry-save kernel); nothing is run.
  */
 thr_status thr_select_variants(const thr_index *idx, uint32_t nq, const uint32_t *id_off,
                                const uint32_t *ids, const uint32_t *T, uint32_t flags,

@@ -502,7 +502,7 @@ def _f32(a) -> np.ndarray:
 
 
 class Selector:
-    """The learned cost model (thr_selector_*): 16 features -> 64 -> 64 -> 3
+    """The learned cost model (thr_selector_*): 16 features -> 64 -> 64 -> 4
     predicted log pass-A times; BF16 weights (FP32 with fp32=True)."""
 
     def __init__(self, seed: int = 0, fp32: bool = False):

@@ -100,6 +100,9 @@ thr_status run_query(const thr_index* idx, const uint32_t* ids, uint32_t n,
     BatchInput in{1, id_off, ids, &T, &var};
     BatchOptions opt;
     opt.profile = profile;
+    // a query of the same shape as an earlier one on this thread replays
+    // that query's CUDA graph (one launch instead of seven stream operations)
+    opt.graph = true;
     BatchStats stats;
     uint64_t off = 0, total = 0;
     TRACE("query n=%u T=%u NG=%u", n, T, idx->NG);
@@ -530,9 +533,12 @@ thr_status thr_select_variants(const thr_index* idx, uint32_t nq, const uint32_t
         resolve_variant(n, T[q], var[q], &cls, &z);
         // the variant that actually runs (fallbacks of ScanCount and split)
         const int fam = class_family(cls);
-        variant[q] = uint8_t(fam == 0 ? kVarCsa : fam == 1 ? kVarScanCount
-                                                : fam == 2 ? kVarPos : fam == 3 ? kVarSplit
-                                                                              : kVarLooped);
+        variant[q] = uint8_t(fam == 0   ? kVarCsa
+                             : fam == 1 ? kVarScanCount
+                             : fam == 2 ? kVarPos
+                             : fam == 3 ? kVarSplit
+                             : fam == 4 ? kVarLooped
+                                        : kVarStaged);
     }
     return THR_OK;
 }

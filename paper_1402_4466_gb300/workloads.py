@@ -12,6 +12,8 @@ concatenated and uploaded with idx_build_rle.
               min(0.3, C k^-1.1) summing to 110 (the mean document length),
               i.i.d.; 4096 queries of N ~ U[10, 200] Zipf-drawn terms with a
               prototype row planted in their N bitmaps, T = ceil(N / 2)
+  sparse      i.i.d. Bernoulli(p) bitmaps (defaults 4096 over 2^24 rows,
+              p = 2e-4), the inputs where ScanCount's per-set-bit cost pays
 """
 from __future__ import annotations
 
@@ -70,3 +72,10 @@ def similarity(nb: int = 1 << 16, r: int = 1 << 24, nq: int = 4096, seed: int = 
     jobs = [(seed, k, r, float(dens[k]), False, planted.get(k)) for k in range(nb)]
     words, offsets = encode_family(jobs, workers)
     return words, offsets, r, queries, protos
+
+
+def sparse(nb: int = 4096, r: int = 1 << 24, p: float = 2e-4, seed: int = 0, workers: int = 0):
+    """(words, offsets) of nb i.i.d. Bernoulli(p) bitmaps over r rows (the
+    very sparse inputs of the counting-variant comparison)."""
+    jobs = [(seed, k, r, float(p), False, None) for k in range(nb)]
+    return encode_family(jobs, workers)

@@ -180,8 +180,8 @@ def test_relaunch_never_reuses_another_index():
 
 
 def test_batch_many_inputs_per_query(mixed):
-    """n above one chunk of input records (128) and above the ScanCount
-    limit (255): the uncached id path and the carry-save fallback."""
+    """n above one chunk of input records (128) and above the 8-bit
+    ScanCount counters (255): the uncached id path and the 16-bit counters."""
     g, o, r = mixed
     rng = np.random.default_rng(8)
     qs = [(rng.integers(0, 48, 300).astype(np.uint32), 140),
