@@ -42,6 +42,15 @@
  * The one device-side wait is a warp's wait for its own bulk copies into
  * shared memory (THR_VARIANT_STAGED); it gives up after about a second, and the
  * call then returns THR_E_TIMEOUT (the results are not valid).
+ *
+ * Checked build: the same library compiled with THR_CHECKED defined
+ * (libthr_checked.so; the Python binding loads it when THR_CHECKED=1 is in
+ * the environment) compares every index-derived global access of the query
+ * kernels of thr_query, thr_query_sym, thr_query_batch, thr_query_static and
+ * the server with the size of what it addresses, skips a failing access and
+ * returns THR_E_CHECK naming the first one.  The opt-threshold profiling
+ * pass and the staged variant's copies are not checked.  Same ABI and
+ * results otherwise.
  */
 #ifndef THR_H
 #define THR_H
@@ -63,7 +72,8 @@ typedef enum {
     THR_E_NOMEM = 3,   /* host or device allocation failed */
     THR_E_NOSPACE = 4, /* output buffer too small; required size returned */
     THR_E_CUDA = 5,    /* a CUDA runtime call failed */
-    THR_E_TIMEOUT = 6  /* a kernel gave up waiting for its shared-memory copies */
+    THR_E_TIMEOUT = 6, /* a kernel gave up waiting for its shared-memory copies */
+    THR_E_CHECK = 7    /* checked build only: an index out of range (access skipped) */
 } thr_status;
 
 /* flags for thr_query / thr_query_batch */

@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 THR_OK, THR_E_INVAL, THR_E_FORMAT, THR_E_NOMEM = 0, 1, 2, 3
-THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT = 4, 5, 6
+THR_E_NOSPACE, THR_E_CUDA, THR_E_TIMEOUT, THR_E_CHECK = 4, 5, 6, 7
 THR_OUT_DEVICE = 0x1
 THR_POLICY_PLAIN, THR_POLICY_RULE, THR_POLICY_LEARNED = 0x00, 0x10, 0x20
 THR_POLICY_MASK = 0xF0
@@ -38,7 +38,7 @@ THR_VARIANT_MASK = 0xE00
 
 STATUS_NAMES = {0: "THR_OK", 1: "THR_E_INVAL", 2: "THR_E_FORMAT",
                 3: "THR_E_NOMEM", 4: "THR_E_NOSPACE", 5: "THR_E_CUDA",
-                6: "THR_E_TIMEOUT"}
+                6: "THR_E_TIMEOUT", 7: "THR_E_CHECK"}
 
 # every symbol include/thr.h declares
 ABI_SYMBOLS = ("idx_build_rle", "thr_query", "thr_query_batch", "thr_query_static", "idx_free",
@@ -64,16 +64,23 @@ class ThrError(RuntimeError):
         self.message = message
 
 
+def checked() -> bool:
+    """THR_CHECKED=1 in the environment selects the checked library
+    (libthr_checked.so: bounds-checked query kernels, THR_E_CHECK)."""
+    return os.environ.get("THR_CHECKED", "") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load():
-    """Build (when missing or stale) and load libthr.so; raises on failure."""
+    """Build (when missing or stale) and load libthr.so (libthr_checked.so
+    with THR_CHECKED=1); raises on failure."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=checked())
             lib = ctypes.CDLL(path)
             u64, u32 = ctypes.c_uint64, ctypes.c_uint32
             vp, u64p, u32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)

@@ -1,5 +1,8 @@
 """Build libthr.so in-tree with nvcc for sm_103a (one -gencode, translation
-units compiled in parallel, no cmake)."""
+units compiled in parallel, no cmake).  build(checked=True) builds the
+checked library, libthr_checked.so (THR_CHECKED defined: every
+index-derived access of the query kernels bounds-checked, THR_E_CHECK on a
+failure), from the same sources into its own object folder."""
 from __future__ import annotations
 
 import glob
@@ -14,6 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libthr.so")
+OUT_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libthr_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-Wall", f"-I{INCLUDE}"]
@@ -38,42 +43,47 @@ def _deps() -> list[str]:
             glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], out: str) -> str:
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
-    if extra and r.stderr:
+    if "-v" in extra and r.stderr:
         print(r.stderr)
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every CUDA/C++ source of the library and link libthr.so."""
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Compile every CUDA/C++ source of the library and link libthr.so (or
+    libthr_checked.so)."""
+    lib, out = (LIB_CHECKED, OUT_CHECKED) if checked else (LIB, OUT)
     with _lock:
-        if not force and not stale():
-            return LIB
-        os.makedirs(OUT, exist_ok=True)
+        if not force and not stale(checked):
+            return lib
+        os.makedirs(out, exist_ok=True)
         extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+        if checked:
+            extra = extra + ["-DTHR_CHECKED"]
         srcs = sources()
         with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-            objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-        tmp = LIB + f".tmp{os.getpid()}"
+            objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
                "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib)
+        return lib
 
 
 if __name__ == "__main__":

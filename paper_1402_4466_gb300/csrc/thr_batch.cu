@@ -369,7 +369,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     const size_t o_memb = o_grp + r256(sizeof(uint2) * nq);
     const size_t plan_bytes = o_memb + r256(sizeof(uint32_t) * std::max<size_t>(memb.size(), 1));
     const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG, launches.size());
-    const size_t res_bytes = 16 * size_t(nq) + 16;
+    const size_t res_bytes = 16 * size_t(nq) + kCtlBytes;
     unsigned char* pin = nullptr;
     CKB(g_ctx.pinned(plan_bytes + r256(res_bytes), &pin), "pinned staging");
     std::memcpy(pin + o_qd, qd.data(), sizeof(QDesc) * nq);
@@ -406,6 +406,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     b.lay = lay;
     b.out = dpool;
     b.cap = cap;
+    b.nids = uint32_t(nids);
+    b.nq = nq;
+    b.nmemb = uint32_t(memb.size());
 
     std::vector<cudaEvent_t> tev;
     PassATimer timer{nullptr};
@@ -430,8 +433,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         e = cudaMemcpyAsync(h_res, b.scratch + lay.res, 16 * size_t(nq), cudaMemcpyDeviceToHost,
                             s);
         if (e != cudaSuccess) return e;
-        // the running output total and the kernels' error word
-        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, 16,
+        // the running output total, the kernels' error word and the check record
+        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, kCtlBytes,
                                cudaMemcpyDeviceToHost, s);
     };
 
@@ -444,6 +447,11 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                      lay.res, lay.full, lay.bagg, lay.bpref, lay.aggs, lay.pref, lay.U, lay.total})
         sig = fnv(sig, v);
     sig = fnv(sig, nq);
+#ifdef THR_CHECKED
+    // the check limits are kernel parameters: a replayed graph must have these
+    sig = fnv(sig, nids);
+    sig = fnv(sig, memb.size());
+#endif
     sig = fnv(sig, reinterpret_cast<uintptr_t>(dmem));
     sig = fnv(sig, reinterpret_cast<uintptr_t>(pin));
     sig = fnv(sig, reinterpret_cast<uintptr_t>(dpool));
@@ -544,6 +552,13 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     if (h_res[2 * size_t(nq) + 1] & 0xFFFFFFFFull)
         return report_error(THR_E_TIMEOUT,
                             "a query kernel gave up waiting for its shared-memory copies");
+    {
+        CheckRec c;
+        std::memcpy(&c, reinterpret_cast<const unsigned char*>(h_res + 2 * size_t(nq)) +
+                            (lay.chk - lay.base),
+                    sizeof c);
+        if (c.site) return check_failed(c);
+    }
     for (uint32_t q = 0; q < nq; ++q) {
         h_off[q] = h_res[2 * size_t(q)];
         h_len[q] = h_res[2 * size_t(q) + 1];

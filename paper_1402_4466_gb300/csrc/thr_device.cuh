@@ -110,6 +110,55 @@ constexpr uint32_t kSymThreshold = 0, kSymRange = 1, kSymOdd = 2;
 // whose T is the current lower bound on the answer.
 constexpr uint32_t kSymProfile = 3;
 
+// Checked builds (compiled with THR_CHECKED): every global access of
+// passes A-C whose index comes from the index arrays or the batch plan (an
+// id, a literal or mask-record address, a slot, a group member, a result
+// position) and every shared-memory record index is compared with the size
+// of what it addresses.  A failing access is skipped and the first one is
+// recorded in the batch scratch (CheckRec: site, index, limit, thread and
+// block), which the host reports as THR_E_CHECK.  Normal builds compile the
+// comparisons away (THR_CHK is true) and never write the record.
+struct CheckRec {
+    uint32_t site, where;       // CheckSite; threadIdx.x | blockIdx.x << 10
+    unsigned long long val, lim;
+};
+enum CheckSite : uint32_t {
+    kChkLiteral = 1,   // a literal word beyond the index's words
+    kChkMask = 2,      // a mask record beyond the index's records
+    kChkIdIndex = 3,   // an id position beyond the batch's ids
+    kChkIdValue = 4,   // an id not below the index's bitmaps
+    kChkSubtile = 5,   // a subtile not below NG
+    kChkRecord = 6,    // a shared-memory input record beyond kCH
+    kChkSlot = 7,      // a slot beyond the chunk's slots or the batch's queries
+    kChkMember = 8,    // a group member position beyond the member list
+    kChkMeta = 9,      // a staged mask record beyond the staging buffer
+    kChkResult = 10,   // a query of pass B or C beyond the batch
+};
+struct CheckLimits {
+    unsigned long long words;  // index words (including the two pad words)
+    unsigned long long masks;  // mask records
+    uint32_t nb;               // bitmaps
+    uint32_t nids;             // ids of the batch
+    uint32_t nq;               // queries of the batch
+    uint32_t slots;            // slots of a chunk
+    uint32_t nmemb;            // group member entries
+};
+#ifdef THR_CHECKED
+__device__ __forceinline__ bool check_access(CheckRec* rec, bool ok, uint32_t site,
+                                             unsigned long long v, unsigned long long lim) {
+    if (!ok && rec && atomicCAS(&rec->site, 0u, site) == 0u) {
+        rec->val = v;
+        rec->lim = lim;
+        rec->where = threadIdx.x | (blockIdx.x << 10);
+    }
+    return ok || !rec;
+}
+#define THR_CHK(rec, cond, site, v, lim) \
+    ::thr::check_access((rec), (cond), (site), (unsigned long long)(v), (unsigned long long)(lim))
+#else
+#define THR_CHK(rec, cond, site, v, lim) true
+#endif
+
 // Pass A of one launch: the queries (slots of the chunk) in list[0..nlist),
 // one work item per (query, subtile), query-major (order 0) or subtile-major
 // (order 1).
@@ -122,6 +171,8 @@ struct PassAParams {
     uint32_t* err;          // set to a non-zero code when a kernel gave up waiting
     uint32_t lose;          // test hook: each staged slot expects 16 bytes more than
                             // it is sent, so its wait runs out (THR_TEST_LOST_COPY)
+    CheckRec* chk;          // checked builds: the first failed check (null: unchecked)
+    CheckLimits lim;        //   and the sizes the checks compare with
     const BitmapDesc* desc;
     const QDesc* qd;        // the chunk's queries, by slot
     const uint32_t* ids;    // every id of the batch
@@ -145,6 +196,8 @@ struct PassAParams {
 // Passes B and C of the re-encoding (thr_reencode.cu), over the Q slots of
 // one chunk; slot s holds query q0 + s of the batch.
 struct WriteParams {
+    CheckRec* chk;      // checked builds: as PassAParams::chk
+    uint32_t chk_nq;    //   queries of the batch
     const uint64_t* U;
     const uint32_t* aggs;
     uint32_t* pref;     // per (slot, subtile): prefix within its scan block

@@ -2,8 +2,10 @@
 #include "thr_exec.h"
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 
+#include "thr_index.h"
 #include "thr_launch.h"
 
 namespace thr {
@@ -56,6 +58,20 @@ uint32_t test_lost_copy() {
     return (v && v[0] == '1') ? 1u : 0u;
 }
 
+thr_status check_failed(const CheckRec& c) {
+    static const char* const names[] = {"?",          "literal word", "mask record",
+                                        "id position", "id value",     "subtile",
+                                        "input record", "slot",        "group member",
+                                        "staged mask record", "result of a query"};
+    char msg[192];
+    std::snprintf(msg, sizeof msg,
+                  "checked build: %s index %llu not below %llu (thread %u, block %u); the "
+                  "access was skipped and the results are not valid",
+                  c.site < sizeof names / sizeof names[0] ? names[c.site] : "?", c.val, c.lim,
+                  c.where & 1023u, c.where >> 10);
+    return report_error(THR_E_CHECK, msg);
+}
+
 uint64_t scratch_per_slot(uint32_t W, uint32_t NG) {
     const uint64_t NB = scan_blocks(NG);
     return 4 + 32 + 2 * 32 * NB + 2 * 32 * uint64_t(NG) + 8 * uint64_t(NG) * kGW;
@@ -69,6 +85,7 @@ ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
     l.gtick = 0;
     l.base = 8;
     l.err = 16;  // a kernel that gave up waiting writes its code here
+    l.chk = 32;  // checked builds: the first failed check (CheckRec)
     l.work = 256;
     l.tick = l.work + r256(4 * nlaunch);
     l.res = l.tick + r256(4 * Q);
@@ -175,6 +192,15 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     p.sseg = idx->d_sseg;
     p.err = reinterpret_cast<uint32_t*>(s + l.err);
     p.lose = test_lost_copy();
+#ifdef THR_CHECKED
+    p.chk = reinterpret_cast<CheckRec*>(s + l.chk);
+    p.lim.words = idx->total_words + 2;
+    p.lim.masks = idx->mixed_subtiles;
+    p.lim.nb = idx->nbitmaps;
+    p.lim.nids = b.nids;
+    p.lim.nq = b.nq;
+    p.lim.nmemb = b.nmemb;
+#endif
     p.desc = idx->d_desc;
     p.ids = b.ids;
     p.W = idx->W;
@@ -183,6 +209,8 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
     p.U = reinterpret_cast<uint64_t*>(s + l.U);
     p.aggs = reinterpret_cast<uint32_t*>(s + l.aggs);
     WriteParams w{};
+    w.chk = p.chk;
+    w.chk_nq = b.nq;
     w.U = p.U;
     w.aggs = p.aggs;
     w.pref = reinterpret_cast<uint32_t*>(s + l.pref);
@@ -203,6 +231,7 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
         p.qd = b.qd + ch.q0;
         p.grp = b.grp + ch.q0;
         p.memb = b.memb;
+        p.lim.slots = ch.Q;
         const uint32_t nl = ch.l1 - ch.l0;
         // several launches run side by side on the aux streams
         const int nside = std::min<int>(int(nl) - 1, std::min(naux, nfork_ev - 1));

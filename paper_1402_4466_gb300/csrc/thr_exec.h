@@ -77,8 +77,12 @@ struct ChunkPlan {
 // Byte offsets of the scratch regions for chunks of at most Q slots and
 // nlaunch pass-A launches in all.
 struct ScratchLayout {
-    size_t gtick, base, err, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
+    size_t gtick, base, err, chk, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
 };
+// The control words the host reads back after a batch: the running output
+// total (at base), the kernels' error word (err) and the check record (chk),
+// kCtlBytes from base.
+constexpr size_t kCtlBytes = 64;
 ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
                              uint64_t nlaunch);
 // Scratch bytes per slot (everything that grows with Q).
@@ -96,6 +100,7 @@ struct ExecBufs {
     ScratchLayout lay;
     uint64_t* out;          // output pool
     uint64_t cap;
+    uint32_t nids = 0, nq = 0, nmemb = 0;  // sizes of ids, qd and memb (checked builds)
 };
 
 // Times of the pass-A launches (THR_PROFILE): an event pair per chunk.
@@ -147,5 +152,9 @@ uint32_t test_lost_copy();
 
 // CTAs per SM of a class's kernel at full occupancy.
 cudaError_t class_occupancy(int cls, int* per_sm);
+
+// THR_E_CHECK with the failed check of a checked build (site, index, limit,
+// thread and block) as the message.
+thr_status check_failed(const CheckRec& c);
 
 }  // namespace thr

@@ -140,6 +140,9 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     b.lay = lay;
     b.out = out;
     b.cap = cap;
+    b.nids = n;
+    b.nq = 1;
+    b.nmemb = 1;
     if ((e = enqueue_plan(idx, &ch, 1, &L, b, st, nullptr, 0, nullptr, 0, nullptr)) !=
         cudaSuccess)
         return cuda_error(e, "launch query kernels");
@@ -150,10 +153,19 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
         (e = cudaMemcpyAsync(&kerr, b.scratch + lay.err, sizeof kerr, cudaMemcpyDeviceToHost,
                              st)) != cudaSuccess)
         return cuda_error(e, "read result length");
+#ifdef THR_CHECKED
+    CheckRec chk{};
+    if ((e = cudaMemcpyAsync(&chk, b.scratch + lay.chk, sizeof chk, cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+        return cuda_error(e, "read check record");
+#endif
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "query");
     if (kerr)
         return report_error(THR_E_TIMEOUT,
                             "a query kernel gave up waiting for its shared-memory copies");
+#ifdef THR_CHECKED
+    if (chk.site) return check_failed(chk);
+#endif
     *out_len = h[1];
     if (*out_len > cap) return report_error(THR_E_NOSPACE, "output buffer too small");
     return THR_OK;

@@ -83,7 +83,10 @@ constexpr size_t cta_smem_bytes() { return sizeof(CtaSmem); }
 // loaded without allocating a line in L1, which keeps the reused packed
 // classes, descriptors and mask records there (3-5% faster pass A on the
 // many-criteria queries).
-__device__ __forceinline__ uint64_t ld_literal(const uint64_t* a) {
+__device__ __forceinline__ uint64_t ld_literal(const PassAParams& p, const uint64_t* a) {
+    if (!THR_CHK(p.chk, uint64_t(a - p.words) < p.lim.words, kChkLiteral, a - p.words,
+                 p.lim.words))
+        return 0;
     uint64_t v;
     asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(a));
     return v;
@@ -99,9 +102,10 @@ __device__ __forceinline__ void stage_masks(const PassAParams& p, WarpSmem& ws, 
         const uint32_t j = (lane >> 2) + 8 * k;
         if (m0 + j < nrec) {
             const uint4 rec = ws.rec[m0 + j];
-            if ((rec.w >> 31) && (part != 2 || ((rec.w >> 30) & 1u))) {
-                const uint4* m = reinterpret_cast<const uint4*>(
-                    p.masks + ((uint64_t(rec.y) << 32) | rec.x));
+            const uint64_t mi = (uint64_t(rec.y) << 32) | rec.x;
+            if ((rec.w >> 31) && (part != 2 || ((rec.w >> 30) & 1u)) &&
+                THR_CHK(p.chk, mi < p.lim.masks, kChkMask, mi, p.lim.masks)) {
+                const uint4* m = reinterpret_cast<const uint4*>(p.masks + mi);
                 ws.meta[j][part] = __ldg(m + part);
             }
         }
@@ -116,6 +120,13 @@ __device__ __forceinline__ void decode_group(const PassAParams& p, WarpSmem& ws,
     const uint32_t bit = 1u << lane;
     const uint32_t lt = bit - 1u;
     const uint32_t mb = r0 % kMetaBatch;  // the group's first slot in the staged batch
+    if (!THR_CHK(p.chk, mb + kGroup <= uint32_t(kMetaBatch), kChkMeta, mb, kMetaBatch)) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) v[j][r] = 0;
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < kGroup; ++j) {
 #pragma unroll
@@ -127,7 +138,7 @@ __device__ __forceinline__ void decode_group(const PassAParams& p, WarpSmem& ws,
             const uint64_t* src = p.words + ra + lane;
 #pragma unroll
             for (int r = 0; r < kRows; ++r)
-                if (x0 + 32 * r + lane < x1) v[j][r] = ld_literal(src + 32 * r);
+                if (x0 + 32 * r + lane < x1) v[j][r] = ld_literal(p, src + 32 * r);
             continue;
         }
         const uint4 lmv = ws.meta[mb + j][0], cmv = ws.meta[mb + j][1], bp = ws.meta[mb + j][3];
@@ -141,14 +152,14 @@ __device__ __forceinline__ void decode_group(const PassAParams& p, WarpSmem& ws,
             for (int r = 0; r < kRows; ++r) {
                 if ((lm[r] | om[r]) == 0u) continue;  // the row is all zero fill
                 const uint32_t off = ((bp.y >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
-                v[j][r] = (lm[r] & bit) ? ld_literal(src + off) : ((om[r] & bit) ? ~0ull : 0ull);
+                v[j][r] = (lm[r] & bit) ? ld_literal(p, src + off) : ((om[r] & bit) ? ~0ull : 0ull);
             }
         } else {
 #pragma unroll
             for (int r = 0; r < kRows; ++r) {
                 if (lm[r] == 0u) continue;  // the row is all zero fill
                 const uint32_t off = ((bp.y >> (8 * r)) & 0xFFu) + __popc(cm[r] & lt);
-                if (lm[r] & bit) v[j][r] = ld_literal(src + off);
+                if (lm[r] & bit) v[j][r] = ld_literal(p, src + off);
             }
         }
     }
@@ -186,9 +197,10 @@ __device__ __forceinline__ void pos_batch(const PassAParams& p, WarpSmem& ws, ui
         const uint32_t j = (lane >> 2) + 8 * k;
         if (j < nb) {
             const uint4 rec = ws.rec[kCH - 1 - (m0 + j)];
-            if (part != 2 || ((rec.w >> 30) & 1u)) {
-                const uint4* m = reinterpret_cast<const uint4*>(
-                    p.masks + ((uint64_t(rec.y) << 32) | rec.x));
+            const uint64_t mi = (uint64_t(rec.y) << 32) | rec.x;
+            if ((part != 2 || ((rec.w >> 30) & 1u)) &&
+                THR_CHK(p.chk, mi < p.lim.masks, kChkMask, mi, p.lim.masks)) {
+                const uint4* m = reinterpret_cast<const uint4*>(p.masks + mi);
                 ws.meta[j][part] = __ldg(m + part);
             }
         }
@@ -230,7 +242,7 @@ __device__ __forceinline__ void pos_batch(const PassAParams& p, WarpSmem& ws, ui
                         const uint32_t cm = reinterpret_cast<const uint32_t*>(&ws.meta[j][1])[r];
                         const uint64_t at = ((uint64_t(m3.w) << 32) | m3.z) +
                                             ((m3.y >> (8 * r)) & 0xFFu) + __popc(cm & lt);
-                        v[k][r] = ld_literal(p.words + at);
+                        v[k][r] = ld_literal(p, p.words + at);
                     }
                 }
             }
@@ -351,11 +363,11 @@ __device__ __forceinline__ uint32_t max_position_count(const PassAParams& p, con
         bool run = false;
         if (j < total) {
             const uint4 rec = kPos ? ws.rec[kCH - 1 - j] : ws.rec[j];
+            const uint64_t mi = (uint64_t(rec.y) << 32) | rec.x;
             if (!(rec.w >> 31)) {
                 run = true;
-            } else {
-                const uint4* m = reinterpret_cast<const uint4*>(
-                    p.masks + ((uint64_t(rec.y) << 32) | rec.x));
+            } else if (THR_CHK(p.chk, mi < p.lim.masks, kChkMask, mi, p.lim.masks)) {
+                const uint4* m = reinterpret_cast<const uint4*>(p.masks + mi);
                 const uint4 lm = __ldg(m);
                 mk[0] = lm.x;
                 mk[1] = lm.y;
@@ -398,9 +410,15 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
         for (uint32_t i0 = 0; i0 < q.n(); i0 += 32) {
             const uint32_t i = i0 + lane;
             uint32_t cls = 0;
-            if (i < q.n())
-                cls = uint32_t(__ldg(p.pcls + uint64_t(__ldg(q.ids() + i)) * p.NGW + (g >> 5)) >>
-                               (2 * (g & 31))) & 3u;
+            if (i < q.n()) {
+                const uint64_t ii = uint64_t(q.ids() + i - p.ids);
+                const uint32_t b = THR_CHK(p.chk, ii < p.lim.nids, kChkIdIndex, ii, p.lim.nids)
+                                       ? __ldg(q.ids() + i)
+                                       : 0u;
+                if (THR_CHK(p.chk, b < p.lim.nb, kChkIdValue, b, p.lim.nb))
+                    cls = uint32_t(__ldg(p.pcls + uint64_t(b) * p.NGW + (g >> 5)) >>
+                                   (2 * (g & 31))) & 3u;
+            }
             k_ones += __popc(__ballot_sync(~0u, cls == 1));
             d_act += __popc(__ballot_sync(~0u, cls >= 2));
         }
@@ -409,18 +427,51 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
     for (uint32_t c0 = 0; c0 < q.n() && !pruned; c0 += kCH) {
         const uint32_t cn = min(uint32_t(kCH), q.n() - c0);
         uint32_t nrec = 0, nrun = 0, nmix = 0;
-        // 1. classify, lane per input, from the subtile descriptor
-        for (uint32_t i0 = 0; i0 < cn; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            uint32_t cls = 0;  // 0 zero fill, 1 ones fill, 2 literal run, 3 mixed
-            uint4 r = make_uint4(0, 0, 0, 0);
+        // 1. classify, lane per input, from the subtile descriptor: the
+        // packed classes of every round of 32 inputs first, then the full
+        // descriptors of the inputs with literals, so that each kind of load
+        // is in flight for all rounds at once (two dependent round trips
+        // per chunk instead of two per round)
+        constexpr int kRounds = kCH / 32;
+        const bool cached = q.cached();
+        const uint32_t* qids = q.ids() + c0;
+        uint32_t cb[kRounds], cc[kRounds];
+#pragma unroll
+        for (int k = 0; k < kRounds; ++k) {
+            const uint32_t i = 32u * k + lane;
+            cb[k] = 0;
+            cc[k] = 0;  // 0 zero fill, 1 ones fill, 2 literal run, 3 mixed
             if (i < cn) {
-                const uint32_t b = q.cached() ? ws.ids[i] : __ldg(q.ids() + c0 + i);
-                // the packed class first; the full descriptor only for inputs with literals
-                cls = uint32_t(__ldg(p.pcls + uint64_t(b) * p.NGW + (g >> 5)) >> (2 * (g & 31))) & 3u;
+                const uint64_t ii = uint64_t(qids + i - p.ids);
+                cb[k] = cached ? ws.ids[i]
+                               : (THR_CHK(p.chk, ii < p.lim.nids, kChkIdIndex, ii, p.lim.nids)
+                                      ? __ldg(qids + i)
+                                      : 0u);
+                if (THR_CHK(p.chk, cb[k] < p.lim.nb, kChkIdValue, cb[k], p.lim.nb) &&
+                    THR_CHK(p.chk, g < p.NG, kChkSubtile, g, p.NG))
+                    cc[k] = uint32_t(__ldg(p.pcls + uint64_t(cb[k]) * p.NGW + (g >> 5)) >>
+                                     (2 * (g & 31))) & 3u;
+            }
+        }
+        uint64_t sdv[kRounds], wov[kRounds];
+#pragma unroll
+        for (int k = 0; k < kRounds; ++k) {
+            sdv[k] = 0;
+            wov[k] = 0;
+            if (cc[k] >= 2) {
+                sdv[k] = __ldg(p.sdesc + uint64_t(cb[k]) * p.NG + g);
+                wov[k] = cached ? ws.woff[32u * k + lane] : p.desc[cb[k]].woff;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRounds; ++k) {
+            if (32u * k >= cn) break;
+            const uint32_t cls = cc[k];
+            uint4 r = make_uint4(0, 0, 0, 0);
+            {
                 if (cls >= 2) {
-                    const uint64_t sd = __ldg(p.sdesc + uint64_t(b) * p.NG + g);
-                    const uint64_t woff = q.cached() ? ws.woff[i] : p.desc[b].woff;
+                    const uint64_t sd = sdv[k];
+                    const uint64_t woff = wov[k];
                     const uint64_t field = sd >> 19;
                     if (cls == 2) {
                         const uint64_t ra = woff + field;
@@ -437,14 +488,19 @@ __device__ __forceinline__ void count_subtile(const PassAParams& p, const QView&
                 const uint32_t a2 = __ballot_sync(~0u, cls == 2);
                 const uint32_t a3 = __ballot_sync(~0u, cls == 3);
                 const uint32_t below = (1u << lane) - 1u;
-                if (cls == 2) ws.rec[nrun + __popc(a2 & below)] = r;
-                if (cls == 3) ws.rec[kCH - 1 - (nmix + __popc(a3 & below))] = r;
+                const uint32_t s2 = nrun + __popc(a2 & below), s3 = nmix + __popc(a3 & below);
+                if (cls == 2 && THR_CHK(p.chk, s2 < uint32_t(kCH), kChkRecord, s2, kCH))
+                    ws.rec[s2] = r;
+                if (cls == 3 && THR_CHK(p.chk, s3 < uint32_t(kCH), kChkRecord, s3, kCH))
+                    ws.rec[kCH - 1 - s3] = r;
                 nrun += __popc(a2);
                 nmix += __popc(a3);
                 nrec = nrun + nmix;
             } else {
                 const uint32_t act = __ballot_sync(~0u, cls >= 2);
-                if (cls >= 2) ws.rec[nrec + __popc(act & ((1u << lane) - 1u))] = r;
+                const uint32_t sr = nrec + __popc(act & ((1u << lane) - 1u));
+                if (cls >= 2 && THR_CHK(p.chk, sr < uint32_t(kCH), kChkRecord, sr, kCH))
+                    ws.rec[sr] = r;
                 nrec += __popc(act);
             }
         }
@@ -658,7 +714,11 @@ __device__ __forceinline__ void load_query(const PassAParams& p, WarpCore& ws, u
     }
     if (n <= uint32_t(kCH)) {
         for (uint32_t i = lane; i < n; i += 32) {
-            const uint32_t b = __ldg(p.ids + ids_off + i);
+            const uint64_t ii = uint64_t(ids_off) + i;
+            uint32_t b = THR_CHK(p.chk, ii < p.lim.nids, kChkIdIndex, ii, p.lim.nids)
+                             ? __ldg(p.ids + ii)
+                             : 0u;
+            if (!THR_CHK(p.chk, b < p.lim.nb, kChkIdValue, b, p.lim.nb)) b = 0;
             ws.ids[i] = b;
             ws.woff[i] = p.desc[b].woff;
         }
@@ -672,6 +732,9 @@ __device__ __forceinline__ void load_query(const PassAParams& p, WarpCore& ws, u
 __device__ __forceinline__ void store_subtile(const PassAParams& p, WarpCore& ws, uint32_t slot,
                                               uint32_t g, uint32_t x0, uint32_t x1,
                                               uint32_t lane, const uint64_t (&orow)[kRows]) {
+    if (!THR_CHK(p.chk, slot < p.lim.slots, kChkSlot, slot, p.lim.slots) ||
+        !THR_CHK(p.chk, g < p.NG, kChkSubtile, g, p.NG))
+        return;
     const uint64_t sg = uint64_t(slot) * p.NG + g;
     // one fill class over all 128 words (words past W are zero): no head and
     // no literal inside, the aggregate follows without the scan
@@ -712,7 +775,9 @@ __device__ __noinline__ void finish_group(const PassAParams& p, WarpCore& ws, ui
                                           uint32_t g, uint32_t x0, uint32_t x1, uint32_t lane,
                                           uint32_t k_ones, uint32_t d_act, Count* count) {
     for (uint32_t i = 0; i < grp.y; ++i) {
+        if (!THR_CHK(p.chk, grp.x + i < p.lim.nmemb, kChkMember, grp.x + i, p.lim.nmemb)) break;
         const uint32_t m = __ldg(p.memb + grp.x + i);
+        if (!THR_CHK(p.chk, m < p.lim.slots, kChkSlot, m, p.lim.slots)) break;
         uint64_t orow[kRows];
         finish_subtile(p, p.qd[m].T, 0u, 0u, kSymThreshold, k_ones, d_act, x0, lane, *count,
                        orow);
@@ -757,7 +822,8 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
             li = it / p.NG;
             g = it - li * p.NG;
         }
-        const uint32_t s = __ldg(p.list + li);
+        uint32_t s = __ldg(p.list + li);
+        if (!THR_CHK(p.chk, s < p.lim.slots, kChkSlot, s, p.lim.slots)) s = 0;
         if (s != cur) {  // a new query: its parameters, and its ids when they fit
             const QDesc d = p.qd[s];
             load_query(p, ws, d.ids_off, d.n, d.Tlo, d.zmode, d.Thi, d.hi, d.sym, lane);
@@ -775,7 +841,11 @@ __device__ __forceinline__ void pass_a(const PassAParams& p, CtaSmem& sm, Count&
             store_subtile(p, ws, cur, g, x0, x1, lane, orow);
         } else if constexpr (Count::kInlineGroups) {  // one count, every member's threshold
             for (uint32_t i = 0; i < grp.y; ++i) {
+                if (!THR_CHK(p.chk, grp.x + i < p.lim.nmemb, kChkMember, grp.x + i,
+                             p.lim.nmemb))
+                    break;
                 const uint32_t m = __ldg(p.memb + grp.x + i);
+                if (!THR_CHK(p.chk, m < p.lim.slots, kChkSlot, m, p.lim.slots)) break;
                 finish_subtile(p, p.qd[m].T, 0u, 0u, kSymThreshold, k_ones, d_act, x0, lane,
                                count, orow);
                 store_subtile(p, ws, m, g, x0, x1, lane, orow);
@@ -840,7 +910,8 @@ __global__ void __launch_bounds__(kNT, 4) k_threshold_split(const PassAParams p)
     uint32_t T = 0, zmode = 0;
     for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
         const uint32_t li = it / p.NG, g = it - li * p.NG;
-        const uint32_t s = __ldg(p.list + li);
+        uint32_t s = __ldg(p.list + li);
+        if (!THR_CHK(p.chk, s < p.lim.slots, kChkSlot, s, p.lim.slots)) s = 0;
         if (s != cur) {  // this warp's share of the new query's inputs
             const QDesc d = p.qd[s];
             const uint32_t a = uint32_t(uint64_t(d.n) * wid / kNW);

@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_aggs(WriteParams w) {
         }
         unsigned long long tot;
         const unsigned long long ex = block_exsum(len, tot);
-        if (t < w.Q) {
+        if (t < w.Q && THR_CHK(w.chk, uint64_t(w.q0) + t < w.chk_nq, kChkResult,
+                               uint64_t(w.q0) + t, w.chk_nq)) {
             const unsigned long long off = run + ex;
             w.res[2 * (uint64_t(w.q0) + t)] = off;
             w.res[2 * (uint64_t(w.q0) + t) + 1] = len;
@@ -247,6 +248,9 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
     if (s >= w.Q) return;
     const uint32_t g = uint32_t(gi - uint64_t(s) * w.NG);
     const uint64_t sg = uint64_t(s) * w.NG + g;
+    if (!THR_CHK(w.chk, uint64_t(w.q0) + s < w.chk_nq, kChkResult, uint64_t(w.q0) + s,
+                 w.chk_nq))
+        return;
     const unsigned long long off = w.res[2 * (uint64_t(w.q0) + s)];
     const uint32_t x0 = g * uint32_t(kGW);
     const uint32_t x1 = min(x0 + uint32_t(kGW), w.W);

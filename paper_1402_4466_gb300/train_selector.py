@@ -1,12 +1,15 @@
 """Train the learned variant selector on timings the kernels produce.
 
 Workloads: the plain and the many-criteria bitmap generators (module
-``synth``) at r = 2^18 .. 2^26 rows, 256 bitmaps each.  A query draws the
-generator (half and half), r = 2^U{18..26}, N log-uniform in [3, 256],
+``synth``) at r = 2^18 .. 2^26 rows, 256 bitmaps each, and very sparse
+inputs: 1024 i.i.d. bitmaps per r with densities log-uniform in
+[5e-5, 2e-3].  A query draws the family (plain 0.4, many-criteria 0.4,
+sparse 0.2), r = 2^U{18..26}, N log-uniform in [3, 256] (sparse: [3, 1024]),
 T uniform in 1..N and N ids with replacement; a query whose result is
 empty is drawn again (at most 20 times).  Its label is, per counting
 variant, the minimum pass-A time of `reps` runs after one warm-up
-(THR_PROFILE), in ms; ScanCount is masked out for N > 255.
+(THR_PROFILE), in ms; a variant that would fall back to the carry-save
+kernel for the query (split above 8 counter bits) is masked out.
 
 Then: features (thr_query_features), normalisation, training of the MLP with
 the library's CUDA kernels (Adam on the squared error of log time), a least
@@ -39,8 +42,10 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 import paper_1402_4466_gb300 as thr  # noqa: E402
+from paper_1402_4466_gb300 import workloads  # noqa: E402
 
 NB = 256
+NB_SPARSE = 1024
 VARIANTS = ("csa", "position", "scancount", "split")
 
 
@@ -70,17 +75,24 @@ def build_indexes(seed, log_rs, workers):
             for name, words in (("plain", plain), ("many", many)):
                 gw, goff = thr.encode_many(words, r)
                 out[(name, lr)] = thr.idx_build_rle(gw, goff, r)
+            sd = synth.log_uniform_densities(seed + 200 + lr, NB_SPARSE, 5e-5, 2e-3)
+            gw, goff = workloads.encode_family(
+                [(seed + 200 + lr, k, r, float(sd[k]), False, None) for k in range(NB_SPARSE)],
+                workers)
+            out[("sparse", lr)] = thr.idx_build_rle(gw, goff, r)
             print(f"  indexes r=2^{lr} built", flush=True)
     return out
 
 
 def draw_query(rng, log_rs):
-    name = "plain" if rng.random() < 0.5 else "many"
+    u = rng.random()
+    name = "plain" if u < 0.4 else ("many" if u < 0.8 else "sparse")
     lr = int(rng.choice(log_rs))
-    n = int(round(math.exp(rng.uniform(math.log(3), math.log(NB)))))
-    n = min(max(n, 3), NB)
+    nb = NB_SPARSE if name == "sparse" else NB
+    n = int(round(math.exp(rng.uniform(math.log(3), math.log(nb)))))
+    n = min(max(n, 3), nb)
     T = int(rng.integers(1, n + 1))
-    ids = rng.integers(0, NB, n).astype(np.uint32)
+    ids = rng.integers(0, nb, n).astype(np.uint32)
     return name, lr, ids, T
 
 
@@ -90,11 +102,10 @@ def measure(idx, ids, T, reps, dout):
     times = np.full(len(VARIANTS), np.nan)
     length = 0
     for v, vf in enumerate(thr.VARIANT_FLAGS):
-        if v == 2 and len(ids) > 255:
+        # the variant the library would run for this flag (ScanCount above
+        # 65535 inputs and split above 8 counter bits fall back to carry-save)
+        if v and int(thr.select_variants(idx, [(ids, T)], vf)[0]) != v:
             continue
-        if v == 3 and max(int(T).bit_length(), 1) > 8 and \
-                int(len(ids) - T + 1).bit_length() > 8:
-            continue  # no split kernel for counters wider than 8 bits
         best = math.inf
         for k in range(reps + 1):
             length = thr.thr_query(idx, ids, T, out=dout, flags=vf | thr.THR_PROFILE)
@@ -183,9 +194,10 @@ def main():
     indexes = build_indexes(0, LOG_R, args.workers)
     for idx in indexes.values():
         # per-bitmap compressed words and set rows for the rule's design matrix
-        n_words = np.zeros(NB)
-        n_bits = np.zeros(NB)
-        for b in range(NB):
+        nb = idx.nbitmaps
+        n_words = np.zeros(nb)
+        n_bits = np.zeros(nb)
+        for b in range(nb):
             f = thr.query_features(idx, [b], 1)
             n_words[b] = 2.0 ** f[9] - 1.0
             n_bits[b] = f[15] * idx.r

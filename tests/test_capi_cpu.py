@@ -163,7 +163,7 @@ def test_binding_constants_match_the_header():
                re.finditer(r"^#define (THR_[A-Z0-9_]+) (0x[0-9A-Fa-f]+|[0-9]+)u?", text, flags=re.M)}
     enums = {m.group(1): int(m.group(2)) for m in
              re.finditer(r"^\s*(THR_(?:OK|E_[A-Z]+)) = ([0-9]+)", text, flags=re.M)}
-    assert len(defines) >= 18 and len(enums) == 7
+    assert len(defines) >= 18 and len(enums) == 8
     sel = {"THR_SEL_FEATURES": thr.SEL_FEATURES, "THR_SEL_VARIANTS": thr.SEL_VARIANTS,
            "THR_SEL_PARAMS": thr.SEL_PARAMS}
     for name, value in {**defines, **enums}.items():
