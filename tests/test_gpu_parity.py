@@ -478,3 +478,22 @@ def test_lost_copy_returns_timeout_and_context_survives(monkeypatch):
     monkeypatch.delenv("THR_TEST_LOST_COPY")
     q.check([0, 1, 2], 2, thr.THR_VARIANT_STAGED)
     p.check([0, 1, 2], 2, thr.THR_VARIANT_STAGED)
+
+
+def test_more_subtiles_than_one_scan_block():
+    """r past 2^26 rows: more than 8192 subtiles, so pass B scans two blocks
+    of subtile aggregates and its last CTA per slot joins them; single
+    queries and a batch of several slots."""
+    r = (1 << 26) + 777_777
+    arrays = [synth.bernoulli(47, 0, r, 0.02), synth.clustered(47, 1, r, 0.3),
+              synth.bernoulli(47, 2, r, 0.2), synth.clustered(47, 3, r, 0.05),
+              synth.rows_to_words(np.arange(r - 5000, r), r), synth.bernoulli(47, 5, r, 1e-4)]
+    p = Pair(arrays, r)
+    assert (synth.nwords(r) + 127) // 128 > 8192
+    for T in (1, 2, 3, 4):
+        p.check(list(range(6)), T)
+    qs = [(np.arange(6, dtype=np.uint32), T) for T in (1, 2, 3)]
+    qs += [(np.array([1, 3, 4], np.uint32), 2), (np.array([0, 0, 2, 5], np.uint32), 2)]
+    off, ln, pool = thr.thr_query_batch(p.g, qs, flags=thr.THR_NO_SHARE)
+    for k, (ids, T) in enumerate(qs):
+        assert np.array_equal(pool[int(off[k]): int(off[k] + ln[k])], p.o.threshold(ids, T)), k
