@@ -100,9 +100,9 @@ def measured_peaks():
 
 
 def ncu_traffic(which: str):
-    """DRAM bytes per launch of a committed ncu capture ("t2": one T = 2
-    query; "step": the batched step's shared counting launch), if it was
-    taken on the current kernel sources."""
+    """DRAM bytes per launch of a committed ncu capture ("t2", "t16", "t32",
+    "t63": one query at that threshold; "step": the batched step's shared
+    counting launch), if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "threshold_kernel_traffic.json")
     if not os.path.exists(p):
         return None
@@ -378,7 +378,8 @@ def run_ours(args):
         km = statistics.median(k_ms_t[T])
         by_t[str(T)] = {"bytes": b, "kernel_ms": round(km, 5),
                         "achieved_gbs": round(b / (km / 1e3) / 1e9, 1),
-                        "frac": round(b / (km / 1e3) / 1e9 / peak, 4)}
+                        "frac": round(b / (km / 1e3) / 1e9 / peak, 4),
+                        "traffic": ncu_traffic(f"t{T}")}
     # the headline: the dense, low-threshold launch (T = 2), where the bytes
     # credited are the bytes the kernel has to read
     dense = by_t[str(Ts[0])]

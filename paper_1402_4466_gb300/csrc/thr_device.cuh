@@ -193,13 +193,6 @@ struct PassAParams {
     const uint32_t* memb;
 };
 
-// Pass B scans the subtile aggregates of a slot in blocks of kScanBlock
-// subtiles, one CTA of kScanThreads threads per block (kScanPer consecutive
-// subtiles per thread): up to 2^26 rows a slot is one block.
-constexpr uint32_t kScanThreads = 1024;
-constexpr uint32_t kScanPer = 8;
-constexpr uint32_t kScanBlock = kScanThreads * kScanPer;
-
 // Passes B and C of the re-encoding (thr_reencode.cu), over the Q slots of
 // one chunk; slot s holds query q0 + s of the batch.
 struct WriteParams {

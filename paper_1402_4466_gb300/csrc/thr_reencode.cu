@@ -68,13 +68,12 @@ __device__ __forceinline__ void warp_scan(RangeAgg& v, bool& have, uint32_t lane
 }
 
 // Pass B, one launch: every CTA scans kScanBlock consecutive aggregates
-// (kScanPer per thread: the thread's total first, a scan of the totals over
-// the CTA, then the thread's subtiles again from that prefix) and stores
-// each subtile's exclusive prefix within the block plus the block's total;
-// the last CTA of a slot to finish (ticket per slot) scans the block totals
-// into block prefixes, and the last slot of the chunk places the results
-// and writes the group that ends at word W.  Pass C joins block prefix and
-// in-block prefix.  Empty values carry kEmpty in cls.
+// (one per thread) and stores each subtile's exclusive prefix within the
+// block plus the block's total; the last CTA to finish (ticket in ctl[4])
+// scans the block totals into block prefixes and writes the group that ends
+// at word W and the total length.  Pass C joins block prefix and in-block
+// prefix.  Empty values carry kEmpty in cls.
+constexpr uint32_t kScanBlock = 256;
 constexpr uint32_t kEmpty = 1u << 8;
 
 __device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t s, uint32_t g) {
@@ -82,10 +81,10 @@ __device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t s, u
     return g == 0 ? fix_first(a) : a;
 }
 
-// Exclusive sum over the CTA (kScanThreads threads) and the total.
+// Exclusive sum over the CTA (kScanBlock threads) and the total.
 __device__ __forceinline__ unsigned long long block_exsum(unsigned long long v,
                                                           unsigned long long& total) {
-    __shared__ unsigned long long wsum[kScanThreads / 32];
+    __shared__ unsigned long long wsum[kScanBlock / 32];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned long long inc = v;
 #pragma unroll
@@ -97,7 +96,7 @@ __device__ __forceinline__ unsigned long long block_exsum(unsigned long long v,
     __syncthreads();
     unsigned long long before = 0;
     total = 0;
-    for (uint32_t k = 0; k < kScanThreads / 32; ++k) {
+    for (uint32_t k = 0; k < kScanBlock / 32; ++k) {
         if (k < wid) before += wsum[k];
         total += wsum[k];
     }
@@ -105,13 +104,13 @@ __device__ __forceinline__ unsigned long long block_exsum(unsigned long long v,
     return before + inc - v;
 }
 
-// Exclusive ordered scan over the CTA (kScanThreads threads); returns the
+// Exclusive ordered scan over the CTA (kScanBlock threads); returns the
 // exclusive prefix of this thread and the block total (in `total`).
 __device__ __forceinline__ RangeAgg block_scan(RangeAgg v, bool vh, bool& eh, RangeAgg& total,
                                                bool& th) {
-    __shared__ RangeAgg wagg[kScanThreads / 32];
-    __shared__ uint32_t whave[kScanThreads / 32];
-    constexpr uint32_t nwarps = kScanThreads / 32;
+    __shared__ RangeAgg wagg[kScanBlock / 32];
+    __shared__ uint32_t whave[kScanBlock / 32];
+    constexpr uint32_t nwarps = kScanBlock / 32;
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     RangeAgg inc = v;
     bool ih = vh;
@@ -154,34 +153,19 @@ __device__ __forceinline__ RangeAgg block_scan(RangeAgg v, bool vh, bool& eh, Ra
     return E;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_aggs(WriteParams w) {
+__global__ void __launch_bounds__(kScanBlock) k_scan_aggs(WriteParams w) {
     const uint32_t s = blockIdx.x / w.NB, b = blockIdx.x - s * w.NB;
-    const uint32_t g0 = b * kScanBlock + threadIdx.x * kScanPer;
-    // the thread's total over its subtiles
-    RangeAgg t{};
-    bool ah = false;
-#pragma unroll
-    for (uint32_t k = 0; k < kScanPer; ++k)
-        if (g0 + k < w.NG) {
-            const RangeAgg a = load_agg(w, s, g0 + k);
-            t = ah ? agg_combine(t, a) : a;
-            ah = true;
-        }
+    const uint32_t g = b * kScanBlock + threadIdx.x;
+    RangeAgg a{};
+    const bool ah = g < w.NG;
+    if (ah) a = load_agg(w, s, g);
     bool eh, th;
     RangeAgg total;
-    RangeAgg E = block_scan(t, ah, eh, total, th);
-    // each subtile's exclusive prefix within the block (its aggregates read
-    // again, now from L2)
-#pragma unroll
-    for (uint32_t k = 0; k < kScanPer; ++k)
-        if (g0 + k < w.NG) {
-            RangeAgg P = E;
-            if (!eh) P.cls = kEmpty;
-            agg_store_plain(w.pref + (uint64_t(s) * w.NG + g0 + k) * kAggWords, P);
-            const RangeAgg a = load_agg(w, s, g0 + k);
-            E = eh ? agg_combine(E, a) : a;
-            eh = true;
-        }
+    RangeAgg E = block_scan(a, ah, eh, total, th);
+    if (ah) {
+        if (!eh) E.cls = kEmpty;
+        agg_store_plain(w.pref + (uint64_t(s) * w.NG + g) * kAggWords, E);
+    }
     __shared__ bool last_block, last_slot;
     if (threadIdx.x == 0) {
         agg_store_plain(w.bagg + (uint64_t(s) * w.NB + b) * kAggWords, total);
@@ -194,7 +178,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_aggs(WriteParams w) {
     // the slot's last CTA: exclusive prefixes of its block totals
     RangeAgg carry{};
     bool ch = false;
-    for (uint32_t b0 = 0; b0 < w.NB; b0 += kScanThreads) {
+    for (uint32_t b0 = 0; b0 < w.NB; b0 += kScanBlock) {
         const uint32_t bb = b0 + threadIdx.x;
         RangeAgg x{};
         const bool xh = bb < w.NB;
@@ -227,7 +211,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_aggs(WriteParams w) {
     // the chunk's last CTA: place the results of its slots in the pool and
     // write the marker of each result's last group
     unsigned long long run = *w.base;
-    for (uint32_t s0 = 0; s0 < w.Q; s0 += kScanThreads) {
+    for (uint32_t s0 = 0; s0 < w.Q; s0 += kScanBlock) {
         const uint32_t t = s0 + threadIdx.x;
         RangeAgg F{};
         unsigned long long len = 0;
@@ -366,7 +350,7 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
 }  // namespace
 
 cudaError_t launch_reencode(const WriteParams& w, cudaStream_t st) {
-    k_scan_aggs<<<uint64_t(w.Q) * w.NB, kScanThreads, 0, st>>>(w);
+    k_scan_aggs<<<uint64_t(w.Q) * w.NB, kScanBlock, 0, st>>>(w);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t warps = uint64_t(w.Q) * w.NG;

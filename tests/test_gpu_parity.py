@@ -480,10 +480,10 @@ def test_lost_copy_returns_timeout_and_context_survives(monkeypatch):
     p.check([0, 1, 2], 2, thr.THR_VARIANT_STAGED)
 
 
-def test_more_subtiles_than_one_scan_block():
-    """r past 2^26 rows: more than 8192 subtiles, so pass B scans two blocks
-    of subtile aggregates and its last CTA per slot joins them; single
-    queries and a batch of several slots."""
+def test_rows_past_two_to_the_26():
+    """r past 2^26 rows (8288 subtiles, 33 pass-B scan blocks per query):
+    single queries and a batch of several slots over clustered, i.i.d.,
+    very sparse and tail-only bitmaps."""
     r = (1 << 26) + 777_777
     arrays = [synth.bernoulli(47, 0, r, 0.02), synth.clustered(47, 1, r, 0.3),
               synth.bernoulli(47, 2, r, 0.2), synth.clustered(47, 3, r, 0.05),
