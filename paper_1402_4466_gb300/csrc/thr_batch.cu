@@ -369,7 +369,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     const size_t o_memb = o_grp + r256(sizeof(uint2) * nq);
     const size_t plan_bytes = o_memb + r256(sizeof(uint32_t) * std::max<size_t>(memb.size(), 1));
     const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG, launches.size());
-    const size_t res_bytes = 16 * size_t(nq) + kCtlBytes;
+    const size_t res_bytes = (lay.res - lay.base) + 16 * size_t(nq);
     unsigned char* pin = nullptr;
     CKB(g_ctx.pinned(plan_bytes + r256(res_bytes), &pin), "pinned staging");
     std::memcpy(pin + o_qd, qd.data(), sizeof(QDesc) * nq);
@@ -377,7 +377,9 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     std::memcpy(pin + o_lists, lists.data(), sizeof(uint32_t) * lists.size());
     std::memcpy(pin + o_grp, grp.data(), sizeof(uint2) * nq);
     if (!memb.empty()) std::memcpy(pin + o_memb, memb.data(), sizeof(uint32_t) * memb.size());
-    unsigned long long* h_res = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
+    // read back from base on: total, error word, check record, then the results
+    unsigned long long* h_ctl = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
+    const unsigned long long* h_res = h_ctl + (lay.res - lay.base) / 8;
 
     if (t0 > 0) t_stage = now_us();
     const bool graph = opt.graph && !opt.profile;
@@ -430,12 +432,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         e = enqueue_plan(idx, chunks.data(), uint32_t(chunks.size()), launches.data(), b, s,
                          g_ctx.aux, kAux, g_ctx.fork, kAux + 1, opt.profile ? &timer : nullptr);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(h_res, b.scratch + lay.res, 16 * size_t(nq), cudaMemcpyDeviceToHost,
-                            s);
-        if (e != cudaSuccess) return e;
-        // the running output total, the kernels' error word and the check record
-        return cudaMemcpyAsync(h_res + 2 * size_t(nq), b.scratch + lay.base, kCtlBytes,
-                               cudaMemcpyDeviceToHost, s);
+        return cudaMemcpyAsync(h_ctl, b.scratch + lay.base, res_bytes, cudaMemcpyDeviceToHost,
+                               s);
     };
 
     // the captured work depends on the plan's shape, the launches, the
@@ -549,13 +547,12 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         }
         if (stats) stats->pass_a_ms = ms;
     }
-    if (h_res[2 * size_t(nq) + 1] & 0xFFFFFFFFull)
+    if (h_ctl[(lay.err - lay.base) / 8] & 0xFFFFFFFFull)
         return report_error(THR_E_TIMEOUT,
                             "a query kernel gave up waiting for its shared-memory copies");
     {
         CheckRec c;
-        std::memcpy(&c, reinterpret_cast<const unsigned char*>(h_res + 2 * size_t(nq)) +
-                            (lay.chk - lay.base),
+        std::memcpy(&c, reinterpret_cast<const unsigned char*>(h_ctl) + (lay.chk - lay.base),
                     sizeof c);
         if (c.site) return check_failed(c);
     }
@@ -563,7 +560,7 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
         h_off[q] = h_res[2 * size_t(q)];
         h_len[q] = h_res[2 * size_t(q) + 1];
     }
-    *total = h_res[2 * size_t(nq)];
+    *total = h_ctl[0];
     return THR_OK;
 }
 

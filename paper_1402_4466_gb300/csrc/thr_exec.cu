@@ -86,10 +86,10 @@ ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
     l.base = 8;
     l.err = 16;  // a kernel that gave up waiting writes its code here
     l.chk = 32;  // checked builds: the first failed check (CheckRec)
-    l.work = 256;
+    l.res = 64;  // right after the control words: one read-back covers both
+    l.work = r256(l.res + 16 * nq);
     l.tick = l.work + r256(4 * nlaunch);
-    l.res = l.tick + r256(4 * Q);
-    l.full = l.res + r256(16 * nq);
+    l.full = l.tick + r256(4 * Q);
     l.bagg = l.full + r256(agg * Q);
     l.bpref = l.bagg + r256(agg * Q * NB);
     l.aggs = l.bpref + r256(agg * Q * NB);
@@ -178,9 +178,9 @@ cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t
                          const PassATimer* timer) {
     const ScratchLayout& l = b.lay;
     unsigned char* s = b.scratch;
-    // control words: chunk ticket, running output offset, work counters,
-    // slot tickets
-    cudaError_t e = cudaMemsetAsync(s, 0, l.res, st);
+    // control words (chunk ticket, running output offset, error word, check
+    // record), the per-query results, work counters and slot tickets
+    cudaError_t e = cudaMemsetAsync(s, 0, l.full, st);
     if (e != cudaSuccess) return e;
     const uint32_t NG = idx->NG;
     PassAParams p{};

@@ -79,10 +79,9 @@ struct ChunkPlan {
 struct ScratchLayout {
     size_t gtick, base, err, chk, work, tick, res, full, bagg, bpref, aggs, pref, U, total;
 };
-// The control words the host reads back after a batch: the running output
-// total (at base), the kernels' error word (err) and the check record (chk),
-// kCtlBytes from base.
-constexpr size_t kCtlBytes = 64;
+// After a batch the host reads back, with one copy from base to the end of
+// res, the running output total (base), the kernels' error word (err), the
+// check record (chk) and every query's {offset, length} (res).
 ScratchLayout scratch_layout(uint64_t Q, uint64_t nq, uint32_t W, uint32_t NG,
                              uint64_t nlaunch);
 // Scratch bytes per slot (everything that grows with Q).

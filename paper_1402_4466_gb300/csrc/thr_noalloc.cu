@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "thr_index.h"
@@ -146,27 +147,21 @@ extern "C" thr_status thr_query_static(const thr_index* idx, const uint32_t* ids
     if ((e = enqueue_plan(idx, &ch, 1, &L, b, st, nullptr, 0, nullptr, 0, nullptr)) !=
         cudaSuccess)
         return cuda_error(e, "launch query kernels");
-    unsigned long long h[2] = {0, 0};
-    uint32_t kerr = 0;
-    if ((e = cudaMemcpyAsync(h, b.scratch + lay.res, sizeof h, cudaMemcpyDeviceToHost, st)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(&kerr, b.scratch + lay.err, sizeof kerr, cudaMemcpyDeviceToHost,
-                             st)) != cudaSuccess)
+    // one read-back from base: total, error word, check record, {offset, length}
+    unsigned long long h[(64 - 8 + 16) / 8] = {};
+    if (lay.res - lay.base + 16 > sizeof h) return report_error(THR_E_CUDA, "control layout");
+    if ((e = cudaMemcpyAsync(h, b.scratch + lay.base, lay.res - lay.base + 16,
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_error(e, "read result length");
-#ifdef THR_CHECKED
-    CheckRec chk{};
-    if ((e = cudaMemcpyAsync(&chk, b.scratch + lay.chk, sizeof chk, cudaMemcpyDeviceToHost,
-                             st)) != cudaSuccess)
-        return cuda_error(e, "read check record");
-#endif
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "query");
-    if (kerr)
+    if (h[(lay.err - lay.base) / 8] & 0xFFFFFFFFull)
         return report_error(THR_E_TIMEOUT,
                             "a query kernel gave up waiting for its shared-memory copies");
-#ifdef THR_CHECKED
+    CheckRec chk;
+    std::memcpy(&chk, reinterpret_cast<const unsigned char*>(h) + (lay.chk - lay.base),
+                sizeof chk);
     if (chk.site) return check_failed(chk);
-#endif
-    *out_len = h[1];
+    *out_len = h[(lay.res - lay.base) / 8 + 1];
     if (*out_len > cap) return report_error(THR_E_NOSPACE, "output buffer too small");
     return THR_OK;
 }
