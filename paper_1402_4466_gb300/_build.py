@@ -5,6 +5,7 @@ index-derived access of the query kernels bounds-checked, THR_E_CHECK on a
 failure), from the same sources into its own object folder."""
 from __future__ import annotations
 
+import fcntl
 import glob
 import os
 import shutil
@@ -70,20 +71,34 @@ def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = Fals
         if not force and not stale(checked):
             return lib
         os.makedirs(out, exist_ok=True)
-        extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-        if checked:
-            extra = extra + ["-DTHR_CHECKED"]
-        srcs = sources()
-        with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-            objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
-        tmp = lib + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
-               "-Xlinker", "--no-undefined"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, lib)
-        return lib
+        # one build at a time across processes too (a process pool whose
+        # workers load the library would otherwise compile into the same
+        # object folder at once); a process that waited finds it built
+        with open(os.path.join(out, ".lock"), "w") as lockf:
+            fcntl.flock(lockf, fcntl.LOCK_EX)
+            try:
+                if not force and not stale(checked):
+                    return lib
+                return _build_locked(lib, out, checked, verbose_ptxas)
+            finally:
+                fcntl.flock(lockf, fcntl.LOCK_UN)
+
+
+def _build_locked(lib: str, out: str, checked: bool, verbose_ptxas: bool) -> str:
+    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    if checked:
+        extra = extra + ["-DTHR_CHECKED"]
+    srcs = sources()
+    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread",
+           "-Xlinker", "--no-undefined"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
