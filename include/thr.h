@@ -304,6 +304,9 @@ thr_status thr_query_static(const thr_index *idx, const uint32_t *ids, uint32_t 
  * the request is done, copies its result (THR_E_NOSPACE if cap is too
  * small, *out_len = its length), gives the time from submit to completion
  * and releases the ticket.  Results equal thr_query's for the same query.
+ * Submitting and waiting may go on at the same time from different host
+ * threads; a ticket is waited for once (a second concurrent wait on the
+ * same ticket returns THR_E_INVAL).
  * thr_server_stats fills 8 counters: queries done, micro-batches run,
  * queries in them, most batches in flight at once, largest batch, most
  * budget bytes claimed at once, requests waiting, batches in flight now.

@@ -45,6 +45,7 @@ struct Request {
     Clock::time_point t_submit, t_start, t_done;
     uint64_t cost = 0;  // bytes claimed from the budget while in flight
     bool done = false;
+    bool waited = false;  // a thr_server_wait call has claimed it
 };
 
 }  // namespace
@@ -263,8 +264,14 @@ thr_status thr_server_wait(thr_server* s, uint64_t ticket, uint64_t* out, uint64
         auto it = s->live.find(ticket);
         if (it == s->live.end()) return report_error(THR_E_INVAL, "unknown ticket");
         r = it->second;
+        if (r->waited)
+            return report_error(THR_E_INVAL, "another thr_server_wait call has this ticket");
+        r->waited = true;
         s->cv_done.wait(lk, [&] { return r->done; });
-        s->live.erase(it);
+        // by key, not by the iterator found before the wait: submissions made
+        // while this thread waited (the lock is released then) may have
+        // rehashed the map and invalidated every iterator into it
+        s->live.erase(ticket);
     }
     const thr_status st = r->status;
     const std::string err = r->error;

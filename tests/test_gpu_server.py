@@ -149,3 +149,41 @@ def test_server_rejects_bad_requests(served):
             srv.wait(t, buf=small)
     finally:
         srv.close()
+
+
+def test_submit_while_waiting(served):
+    """One thread submits while another waits, as a serving front end does:
+    the table of live tickets grows (and rehashes) while waits are blocked
+    on it.  Every result equals the same query run alone, and a sample the
+    oracle's."""
+    g, o, r = served
+    rng = np.random.default_rng(37)
+    reqs = []
+    for _ in range(3000):
+        n = int(rng.integers(2, 40))
+        reqs.append((rng.integers(0, 64, n).astype(np.uint32), int(rng.integers(1, n + 1))))
+    srv = thr.Server(g, workers=4, max_batch=16)
+    tickets = [None] * len(reqs)
+    got = [None] * len(reqs)
+
+    def submitter():
+        for i, (ids, T) in enumerate(reqs):
+            tickets[i] = srv.submit(ids, T)
+            if i % 50 == 0:
+                time.sleep(0.0005)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    try:
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            got[i] = srv.wait(tickets[i])[0]
+    finally:
+        th.join()
+        srv.close()
+    for i, (ids, T) in enumerate(reqs):
+        assert np.array_equal(got[i], thr.thr_query(g, ids, T)), i
+    for i in range(0, len(reqs), 60):
+        ids, T = reqs[i]
+        assert np.array_equal(got[i], o.threshold(ids, T)), i
