@@ -52,6 +52,7 @@ struct ThreadCtx {
     int device = -1;
     unsigned char* pin = nullptr;
     size_t pin_bytes = 0;
+    size_t pin_grown = 0;  // size of the last allocation (growth is geometric)
     cudaStream_t aux[kAux] = {};
     cudaEvent_t fork[kAux + 1] = {};
     cudaEvent_t join_in = nullptr;  // orders the capture stream after the caller's
@@ -79,13 +80,16 @@ struct ThreadCtx {
         ok = true;
         return cudaSuccess;
     }
-    void release() {
-        if (!ok) return;
+    void drop_graphs() {
         for (auto& g : graphs)
             if (g.exec) {
                 cudaGraphExecDestroy(g.exec);
                 g = GraphSlot{};
             }
+    }
+    void release() {
+        if (!ok) return;
+        drop_graphs();
         for (int k = 0; k < kAux; ++k) cudaStreamDestroy(aux[k]);
         for (int k = 0; k <= kAux; ++k) cudaEventDestroy(fork[k]);
         cudaEventDestroy(join_in);
@@ -94,12 +98,22 @@ struct ThreadCtx {
     }
     cudaError_t pinned(size_t bytes, unsigned char** out) {
         if (pin_bytes < bytes) {
+            // Every cached graph copies to and from this buffer, and the
+            // copy nodes keep the mapping of the allocation they were made
+            // with.  A new allocation can come back at the same address (so
+            // a graph's signature would still match), and replaying such a
+            // graph would copy through the freed allocation's mapping: a
+            // host crash or a GPU fault.  So the graphs go first.  The buffer
+            // grows at least twofold, in whole 64 KiB, so that this is rare.
+            drop_graphs();
             if (pin) cudaFreeHost(pin);
             pin = nullptr;
             pin_bytes = 0;
-            cudaError_t e = cudaMallocHost(&pin, bytes);
+            const size_t want = (std::max(bytes, 2 * pin_grown) + 65535) & ~size_t(65535);
+            cudaError_t e = cudaMallocHost(&pin, want);
             if (e != cudaSuccess) return e;
-            pin_bytes = bytes;
+            pin_bytes = want;
+            pin_grown = want;
         }
         *out = pin;
         return cudaSuccess;
