@@ -1,6 +1,7 @@
 """GPU tests of the serving loop (thr_server_*): with continuous batching,
 every result equals the same query run alone (thr_query) and the CPU
-oracle's; requests that arrive while others run join later micro-batches;
+oracle's, also with submissions and waits on different threads and with
+single queries whose staging grows between cached graphs; requests that arrive while others run join later micro-batches;
 micro-batches of several workers are in flight at once; the memory budget
 bounds what is admitted; a budget smaller than one request still serves
 every request, one at a time."""
@@ -187,3 +188,13 @@ def test_submit_while_waiting(served):
     for i in range(0, len(reqs), 60):
         ids, T = reqs[i]
         assert np.array_equal(got[i], o.threshold(ids, T)), i
+
+
+def test_single_queries_while_staging_grows(served):
+    """One thread, many single queries of varying size: the pinned staging
+    a thread's calls share grows several times while graphs of earlier
+    shapes are cached and later replayed (a new staging allocation can come
+    back at the old address).  Every result equals the oracle's."""
+    g, o, r = served
+    for ids, T in _requests(1, 120):
+        assert np.array_equal(thr.thr_query(g, ids, T), o.threshold(ids, T)), (len(ids), T)
