@@ -7,7 +7,7 @@
 // classes).  Pass B scans each slot's aggregates in order (word 0 of a
 // bitmap always starts the first group) into the prefix before every
 // subtile and the aggregate of the whole result, whose heads + literals are
-// the encoded length; the last CTA of the chunk then scans the lengths over
+// the encoded length; the last warp of the chunk then scans the lengths over
 // the slots, which places each result in the output pool after those of the
 // earlier slots and chunks, and writes each result's final marker (the group
 // that ends at word W).  Pass C gives every literal and every marker whose
@@ -67,13 +67,19 @@ __device__ __forceinline__ void warp_scan(RangeAgg& v, bool& have, uint32_t lane
     }
 }
 
-// Pass B, one launch: every CTA scans kScanBlock consecutive aggregates
-// (one per thread) and stores each subtile's exclusive prefix within the
-// block plus the block's total; the last CTA to finish (ticket in ctl[4])
-// scans the block totals into block prefixes and writes the group that ends
-// at word W and the total length.  Pass C joins block prefix and in-block
-// prefix.  Empty values carry kEmpty in cls.
+// Pass B, one launch, one warp per scan block of kScanBlock consecutive
+// subtiles of a slot: each lane loads its kPer consecutive aggregates at
+// once, the lanes' totals are scanned across the warp, and every subtile's
+// exclusive prefix within the block (kEmpty in cls for the block's first
+// subtile) and the block's total are stored.  The warp that takes the slot's
+// last ticket (tick) then scans the slot's block totals into block prefixes
+// and the aggregate of the whole result, and the warp that takes the
+// chunk's last ticket (gtick) places the chunk's results in the pool and
+// writes each one's final marker (the group that ends at word W).  The
+// tickets only select who finishes: no warp waits for another.  Pass C
+// joins block prefix and in-block prefix.
 constexpr uint32_t kScanBlock = 256;
+constexpr uint32_t kPer = kScanBlock / 32;  // subtiles per lane
 constexpr uint32_t kEmpty = 1u << 8;
 
 __device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t s, uint32_t g) {
@@ -81,149 +87,119 @@ __device__ __forceinline__ RangeAgg load_agg(const WriteParams& w, uint32_t s, u
     return g == 0 ? fix_first(a) : a;
 }
 
-// Exclusive sum over the CTA (kScanBlock threads) and the total.
-__device__ __forceinline__ unsigned long long block_exsum(unsigned long long v,
-                                                          unsigned long long& total) {
-    __shared__ unsigned long long wsum[kScanBlock / 32];
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long inc = v;
+// An aggregate another warp of this launch stored: read through L2.
+__device__ __forceinline__ RangeAgg agg_load_l2(const uint32_t* p) {
+    const uint4 x = __ldcg(reinterpret_cast<const uint4*>(p));
+    const uint2 y = __ldcg(reinterpret_cast<const uint2*>(p + 4));
+    RangeAgg a;
+    a.start = x.x;
+    a.nh = x.y;
+    a.nl = x.z;
+    a.lh = x.w;
+    a.lp = y.x;
+    a.cls = y.y;
+    return a;
+}
+
+__global__ void __launch_bounds__(kNT) k_scan_aggs(WriteParams w) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wi = uint64_t(blockIdx.x) * kNW + (threadIdx.x >> 5);
+    const uint32_t NG = w.NG, NB = w.NB;
+    if (wi >= uint64_t(w.Q) * NB) return;  // the whole warp
+    const uint32_t s = uint32_t(wi / NB), blk = uint32_t(wi - uint64_t(s) * NB);
+    const uint32_t g0 = blk * kScanBlock + kPer * lane;
+    // 1. the block
+    RangeAgg a[kPer];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long t = __shfl_up_sync(~0u, inc, d);
-        if (lane >= uint32_t(d)) inc += t;
-    }
-    if (lane == 31) wsum[wid] = inc;
-    __syncthreads();
-    unsigned long long before = 0;
-    total = 0;
-    for (uint32_t k = 0; k < kScanBlock / 32; ++k) {
-        if (k < wid) before += wsum[k];
-        total += wsum[k];
-    }
-    __syncthreads();
-    return before + inc - v;
-}
-
-// Exclusive ordered scan over the CTA (kScanBlock threads); returns the
-// exclusive prefix of this thread and the block total (in `total`).
-__device__ __forceinline__ RangeAgg block_scan(RangeAgg v, bool vh, bool& eh, RangeAgg& total,
-                                               bool& th) {
-    __shared__ RangeAgg wagg[kScanBlock / 32];
-    __shared__ uint32_t whave[kScanBlock / 32];
-    constexpr uint32_t nwarps = kScanBlock / 32;
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    RangeAgg inc = v;
-    bool ih = vh;
+    for (uint32_t i = 0; i < kPer; ++i)
+        if (g0 + i < NG) a[i] = load_agg(w, s, g0 + i);
+    RangeAgg inc{};
+    bool ih = false;
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i)
+        if (g0 + i < NG) {
+            inc = ih ? agg_combine(inc, a[i]) : a[i];
+            ih = true;
+        }
     warp_scan(inc, ih, lane);
-    if (lane == 31) {
-        wagg[wid] = inc;
-        whave[wid] = ih;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        RangeAgg x = lane < nwarps ? wagg[lane] : RangeAgg{};
-        bool xh = lane < nwarps && whave[lane] != 0;
-        warp_scan(x, xh, lane);
-        const RangeAgg ex = shfl_up_agg(x, 1);
-        const uint32_t xh_up = __shfl_up_sync(~0u, xh ? 1u : 0u, 1);  // every lane
-        const RangeAgg last = shfl_down_last(x, nwarps - 1);
-        const uint32_t lasth = __shfl_sync(~0u, xh ? 1u : 0u, nwarps - 1);
-        __syncwarp();
-        if (lane < nwarps) {
-            wagg[lane] = ex;
-            whave[lane] = lane > 0 && xh_up != 0u;
+    RangeAgg E = shfl_up_agg(inc, 1);
+    bool eh = __shfl_up_sync(~0u, ih ? 1u : 0u, 1) != 0u && lane > 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kPer; ++i)
+        if (g0 + i < NG) {
+            RangeAgg out = E;
+            if (!eh) out.cls = kEmpty;
+            agg_store_plain(w.pref + (uint64_t(s) * NG + g0 + i) * kAggWords, out);
+            E = eh ? agg_combine(E, a[i]) : a[i];
+            eh = true;
         }
-        if (lane == 0) {
-            wagg[0] = last;  // slot 0's exclusive prefix is empty: reuse it for the total
-            whave[0] = lasth ? 2u : 0u;
-        }
-    }
-    __syncthreads();
-    total = wagg[0];
-    th = (whave[0] & 2u) != 0;
-    RangeAgg E = wagg[wid];
-    eh = wid > 0 && (whave[wid] & 1u) != 0;
-    const RangeAgg le = shfl_up_agg(inc, 1);
-    const uint32_t ih_up = __shfl_up_sync(~0u, ih ? 1u : 0u, 1);  // every lane
-    if (lane > 0 && ih_up != 0u) {
-        E = eh ? agg_combine(E, le) : le;
-        eh = true;
-    }
-    __syncthreads();
-    return E;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_scan_aggs(WriteParams w) {
-    const uint32_t s = blockIdx.x / w.NB, b = blockIdx.x - s * w.NB;
-    const uint32_t g = b * kScanBlock + threadIdx.x;
-    RangeAgg a{};
-    const bool ah = g < w.NG;
-    if (ah) a = load_agg(w, s, g);
-    bool eh, th;
-    RangeAgg total;
-    RangeAgg E = block_scan(a, ah, eh, total, th);
-    if (ah) {
-        if (!eh) E.cls = kEmpty;
-        agg_store_plain(w.pref + (uint64_t(s) * w.NG + g) * kAggWords, E);
-    }
-    __shared__ bool last_block, last_slot;
-    if (threadIdx.x == 0) {
-        agg_store_plain(w.bagg + (uint64_t(s) * w.NB + b) * kAggWords, total);
+    const RangeAgg total = shfl_down_last(inc, 31);
+    uint32_t last = 0;
+    if (lane == 0) {
+        agg_store_plain(w.bagg + (uint64_t(s) * NB + blk) * kAggWords, total);
         __threadfence();
-        last_block = atomicAdd(w.tick + s, 1u) == w.NB - 1;
+        last = atomicAdd(w.tick + s, 1u) == NB - 1 ? 1u : 0u;
     }
-    __syncthreads();
-    if (!last_block) return;
+    if (!__shfl_sync(~0u, last, 0)) return;
     __threadfence();
-    // the slot's last CTA: exclusive prefixes of its block totals
+    // 2. the slot's last warp: exclusive prefixes of its block totals, 32 at
+    // a time with the earlier ones carried
     RangeAgg carry{};
     bool ch = false;
-    for (uint32_t b0 = 0; b0 < w.NB; b0 += kScanBlock) {
-        const uint32_t bb = b0 + threadIdx.x;
+    for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
+        const uint32_t bb = b0 + lane;
         RangeAgg x{};
-        const bool xh = bb < w.NB;
-        if (xh) x = agg_load_plain(w.bagg + (uint64_t(s) * w.NB + bb) * kAggWords);
-        bool ebh, cth;
-        RangeAgg ctot;
-        RangeAgg Eb = block_scan(x, xh, ebh, ctot, cth);
-        if (ch) {  // prepend the totals of the earlier block groups
-            Eb = ebh ? agg_combine(carry, Eb) : carry;
+        bool xh = bb < NB;
+        if (xh) x = agg_load_l2(w.bagg + (uint64_t(s) * NB + bb) * kAggWords);
+        warp_scan(x, xh, lane);
+        const RangeAgg ex = shfl_up_agg(x, 1);
+        const bool exh = __shfl_up_sync(~0u, xh ? 1u : 0u, 1) != 0u && lane > 0;
+        RangeAgg Eb = carry;
+        bool ebh = ch;
+        if (exh) {
+            Eb = ch ? agg_combine(carry, ex) : ex;
             ebh = true;
         }
-        if (xh) {
+        if (bb < NB) {
             if (!ebh) Eb.cls = kEmpty;
-            agg_store_plain(w.bpref + (uint64_t(s) * w.NB + bb) * kAggWords, Eb);
+            agg_store_plain(w.bpref + (uint64_t(s) * NB + bb) * kAggWords, Eb);
         }
-        if (cth) {
-            carry = ch ? agg_combine(carry, ctot) : ctot;
+        const RangeAgg tot = shfl_down_last(x, 31);
+        if (__shfl_sync(~0u, xh ? 1u : 0u, 31)) {
+            carry = ch ? agg_combine(carry, tot) : tot;
             ch = true;
         }
     }
-    if (threadIdx.x == 0) {  // carry covers the whole result of slot s
+    last = 0;
+    if (lane == 0) {  // carry covers the whole result of slot s
         agg_store_plain(w.full + uint64_t(s) * kAggWords, carry);
         w.tick[s] = 0;
         __threadfence();
-        last_slot = atomicAdd(w.gtick, 1u) == w.Q - 1;
+        last = atomicAdd(w.gtick, 1u) == w.Q - 1 ? 1u : 0u;
     }
-    __syncthreads();
-    if (!last_slot) return;
+    if (!__shfl_sync(~0u, last, 0)) return;
     __threadfence();
-    // the chunk's last CTA: place the results of its slots in the pool and
-    // write the marker of each result's last group
-    unsigned long long run = *w.base;
-    for (uint32_t s0 = 0; s0 < w.Q; s0 += kScanBlock) {
-        const uint32_t t = s0 + threadIdx.x;
+    // 3. the chunk's last warp: place the results of its slots in the pool
+    // and write the marker of each result's last group
+    unsigned long long run = __ldcg(w.base);
+    for (uint32_t s0 = 0; s0 < w.Q; s0 += 32) {
+        const uint32_t t = s0 + lane;
         RangeAgg F{};
         unsigned long long len = 0;
         if (t < w.Q) {
-            F = agg_load_plain(w.full + uint64_t(t) * kAggWords);
+            F = agg_load_l2(w.full + uint64_t(t) * kAggWords);
             len = uint64_t(F.nh) + F.nl;
         }
-        unsigned long long tot;
-        const unsigned long long ex = block_exsum(len, tot);
+        unsigned long long incl = len;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const unsigned long long u = __shfl_up_sync(~0u, incl, d);
+            if (lane >= d) incl += u;
+        }
+        const unsigned long long tot = __shfl_sync(~0u, incl, 31);
         if (t < w.Q && THR_CHK(w.chk, uint64_t(w.q0) + t < w.chk_nq, kChkResult,
                                uint64_t(w.q0) + t, w.chk_nq)) {
-            const unsigned long long off = run + ex;
+            const unsigned long long off = run + incl - len;
             w.res[2 * (uint64_t(w.q0) + t)] = off;
             w.res[2 * (uint64_t(w.q0) + t) + 1] = len;
             const uint64_t L = uint64_t(F.nl) - F.lp;
@@ -234,7 +210,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_aggs(WriteParams w) {
         }
         run += tot;
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         *w.base = run;
         *w.gtick = 0;
     }
@@ -350,7 +326,8 @@ __global__ void __launch_bounds__(kNT) k_write_out(WriteParams w) {
 }  // namespace
 
 cudaError_t launch_reencode(const WriteParams& w, cudaStream_t st) {
-    k_scan_aggs<<<uint64_t(w.Q) * w.NB, kScanBlock, 0, st>>>(w);
+    const uint64_t blocks = uint64_t(w.Q) * w.NB;  // one warp each
+    k_scan_aggs<<<(blocks + kNW - 1) / kNW, kNT, 0, st>>>(w);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t warps = uint64_t(w.Q) * w.NG;
