@@ -136,20 +136,6 @@ uint64_t fnv(uint64_t h, uint64_t v) {
     return h;
 }
 
-// THR_TRACE_TIME=1 in the environment: one stderr line per batch call with
-// the host time (us) at the end of planning, staging, launch and the wait.
-bool trace_time_on() {
-    static const bool on = [] {
-        const char* v = std::getenv("THR_TRACE_TIME");
-        return v && v[0] == '1';
-    }();
-    return on;
-}
-double now_us() {
-    return std::chrono::duration<double, std::micro>(
-               std::chrono::steady_clock::now().time_since_epoch())
-        .count();
-}
 
 uint64_t env_u64(const char* name, uint64_t dflt) {
     const char* v = std::getenv(name);
@@ -233,6 +219,19 @@ void form_groups(const BatchInput& in, uint32_t q0, uint32_t Q, std::vector<QDes
 }
 
 }  // namespace
+
+bool trace_time_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("THR_TRACE_TIME");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+double now_us() {
+    return std::chrono::duration<double, std::micro>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
 
 thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool, uint64_t cap,
                      uint64_t* h_off, uint64_t* h_len, uint64_t* total, cudaStream_t st,
@@ -384,15 +383,19 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     const size_t plan_bytes = o_memb + r256(sizeof(uint32_t) * std::max<size_t>(memb.size(), 1));
     const ScratchLayout lay = scratch_layout(Qmax, nq, W, NG, launches.size());
     const size_t res_bytes = (lay.res - lay.base) + 16 * size_t(nq);
+    // the plan and, right after it (where the scratch starts on the device),
+    // the zeroed control words go up in one copy: no memset node
+    const size_t up_bytes = plan_bytes + lay.full;
     unsigned char* pin = nullptr;
-    CKB(g_ctx.pinned(plan_bytes + r256(res_bytes), &pin), "pinned staging");
+    CKB(g_ctx.pinned(r256(up_bytes) + r256(res_bytes), &pin), "pinned staging");
+    std::memset(pin + plan_bytes, 0, lay.full);
     std::memcpy(pin + o_qd, qd.data(), sizeof(QDesc) * nq);
     std::memcpy(pin + o_ids, in.ids, sizeof(uint32_t) * nids);
     std::memcpy(pin + o_lists, lists.data(), sizeof(uint32_t) * lists.size());
     std::memcpy(pin + o_grp, grp.data(), sizeof(uint2) * nq);
     if (!memb.empty()) std::memcpy(pin + o_memb, memb.data(), sizeof(uint32_t) * memb.size());
     // read back from base on: total, error word, check record, then the results
-    unsigned long long* h_ctl = reinterpret_cast<unsigned long long*>(pin + plan_bytes);
+    unsigned long long* h_ctl = reinterpret_cast<unsigned long long*>(pin + r256(up_bytes));
     const unsigned long long* h_res = h_ctl + (lay.res - lay.base) / 8;
 
     if (t0 > 0) t_stage = now_us();
@@ -441,10 +444,11 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
     } ev_guard{tev};
 
     auto enqueue = [&](cudaStream_t s) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(dmem, pin, plan_bytes, cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(dmem, pin, up_bytes, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return e;
         e = enqueue_plan(idx, chunks.data(), uint32_t(chunks.size()), launches.data(), b, s,
-                         g_ctx.aux, kAux, g_ctx.fork, kAux + 1, opt.profile ? &timer : nullptr);
+                         g_ctx.aux, kAux, g_ctx.fork, kAux + 1, opt.profile ? &timer : nullptr,
+                         true);
         if (e != cudaSuccess) return e;
         return cudaMemcpyAsync(h_ctl, b.scratch + lay.base, res_bytes, cudaMemcpyDeviceToHost,
                                s);

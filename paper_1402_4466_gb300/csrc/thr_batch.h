@@ -61,6 +61,12 @@ uint32_t tune_lookup(const thr_index* idx, uint32_t key);
 // Run a batch with results into the device pool dpool (cap words); h_off,
 // h_len receive each query's place and length, *total the words needed.
 // Words past cap are not written.  Synchronous.
+// THR_TRACE_TIME=1 in the environment: one stderr line per batch call with
+// the host time (us) at the end of planning, staging, launch and the wait
+// (and, from thr_query_batch, of its argument checks and variant choice).
+bool trace_time_on();
+double now_us();
+
 thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool, uint64_t cap,
                      uint64_t* h_off, uint64_t* h_len, uint64_t* total, cudaStream_t st,
                      const BatchOptions& opt, BatchStats* stats);

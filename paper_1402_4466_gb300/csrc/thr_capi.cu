@@ -696,9 +696,11 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
     if (flags & ~(THR_OUT_DEVICE | THR_POLICY_MASK | THR_PROFILE | THR_VARIANT_MASK |
                   THR_NO_GRAPH | THR_NO_SHARE))
         return fail(THR_E_INVAL, "unknown flags");
+    const double t_in = trace_time_on() ? now_us() : 0.0;
     std::vector<uint8_t> cls;
     thr_status ps = check_batch(idx, nq, id_off, ids, T, flags, &cls);
     if (ps != THR_OK) return ps;
+    if (t_in > 0) std::fprintf(stderr, "[thr] batch checks and variants %.1f us\n", now_us() - t_in);
     BatchInput in{nq, id_off, ids, T, cls.data()};
     BatchOptions opt;
     opt.graph = !(flags & THR_NO_GRAPH);
@@ -708,8 +710,10 @@ thr_status thr_query_batch(const thr_index* idx, uint32_t nq, const uint32_t* id
     cudaStream_t st = (cudaStream_t)cuda_stream;
     uint64_t total = 0;
     if (flags & THR_OUT_DEVICE) {
+        const double t_p = trace_time_on() ? now_us() : 0.0;
         if (pool_cap > 0 && !is_device_ptr(pool, idx->device))
             return fail(THR_E_INVAL, "THR_OUT_DEVICE given but pool is not device memory");
+        if (t_p > 0) std::fprintf(stderr, "[thr] batch pool check %.1f us\n", now_us() - t_p);
         thr_status s = run_batch(idx, in, pool, pool_cap, out_off, out_len, &total, st, opt,
                                  &stats);
         if (s != THR_OK) return s;

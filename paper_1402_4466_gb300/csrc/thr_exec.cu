@@ -175,12 +175,12 @@ cudaError_t class_occupancy(int cls, int* per_sm) {
 cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,
                          const Launch* launches, const ExecBufs& b, cudaStream_t st,
                          cudaStream_t* aux, int naux, cudaEvent_t* fork_ev, int nfork_ev,
-                         const PassATimer* timer) {
+                         const PassATimer* timer, bool zeroed) {
     const ScratchLayout& l = b.lay;
     unsigned char* s = b.scratch;
     // control words (chunk ticket, running output offset, error word, check
     // record), the per-query results, work counters and slot tickets
-    cudaError_t e = cudaMemsetAsync(s, 0, l.full, st);
+    cudaError_t e = zeroed ? cudaSuccess : cudaMemsetAsync(s, 0, l.full, st);
     if (e != cudaSuccess) return e;
     const uint32_t NG = idx->NG;
     PassAParams p{};

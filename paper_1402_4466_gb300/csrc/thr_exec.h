@@ -111,10 +111,12 @@ struct PassATimer {
 // pass-A launches (forked onto the aux streams when there are several),
 // pass B and pass C.  Results: res (offset, length per query) and base
 // (total words) in scratch.  aux: naux streams for the forks (may be 0).
+// zeroed: the caller's copy of the plan already zeroed the control words
+// (the ScratchLayout up to `full`), so no memset is enqueued.
 cudaError_t enqueue_plan(const thr_index* idx, const ChunkPlan* chunks, uint32_t nchunks,
                          const Launch* launches, const ExecBufs& b, cudaStream_t st,
                          cudaStream_t* aux, int naux, cudaEvent_t* fork_ev, int nfork_ev,
-                         const PassATimer* timer);
+                         const PassATimer* timer, bool zeroed = false);
 
 // Counting variants a query can run with (the selector's choices):
 //   kVarCsa        carry-save bit slices, inputs decoded in groups of four;
