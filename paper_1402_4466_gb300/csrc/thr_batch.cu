@@ -143,6 +143,19 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
     return std::strtoull(v, nullptr, 10);
 }
 
+// Does a query classify its inputs from their subtile descriptors alone
+// (QDesc::direct)?  When most of its inputs hold literals in most subtiles:
+// an input's share of subtiles with literals is estimated as min(1, stream
+// words / subtiles), and the shares must add up to half the inputs.  Else
+// the packed classes keep the zero-fill inputs from costing a descriptor
+// load each.
+bool direct_classification(const thr_index* idx, const uint32_t* ids, uint32_t n) {
+    double share = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        share += std::min(1.0, double(idx->desc[ids[i]].len) / double(idx->NG));
+    return 2.0 * share >= double(n);
+}
+
 // Groups among the chunk's grouped-carry-save queries over the same id
 // multiset: the first member leads, counts ones with enough slices for the
 // group's largest threshold and prunes only subtiles decided for every
@@ -283,7 +296,8 @@ thr_status run_batch(const thr_index* idx, const BatchInput& in, uint64_t* dpool
                 }
             z = 0;
         }
-        qd[q] = QDesc{in.id_off[q], n, in.T[q], z, in.T[q], in.T[q], hi, sym};
+        qd[q] = QDesc{in.id_off[q], n, in.T[q], z, in.T[q], in.T[q], hi, sym, 0u};
+        qd[q].direct = direct_classification(idx, in.ids + in.id_off[q], n) ? 1u : 0u;
         qcls[q] = uint8_t(cls);
     }
     // groups of queries over the same id multiset (grouped carry-save, same

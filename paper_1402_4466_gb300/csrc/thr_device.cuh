@@ -102,6 +102,8 @@ struct QDesc {
     uint32_t Tlo, Thi;
     uint32_t hi;       // range queries: the upper bound
     uint32_t sym;      // kSymThreshold, kSymRange, kSymOdd (or kSymProfile)
+    uint32_t direct;   // 1: classify from the subtile descriptors alone
+                       //   (most inputs hold literals in most subtiles)
 };
 // What a query computes from the count c of a row: c >= T (threshold),
 // T <= c <= hi (range: at most, exactly, between), c odd (the XOR).

@@ -29,8 +29,8 @@
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                 \
             blocks, k_threshold<S, POS>, kNT, cta_smem_bytes());              \
     }
-#define THR_DEFINE_WIDTH(S) THR_DEFINE_KERNEL(S, false, threshold)
-#define THR_DEFINE_WIDTH_POS(S) THR_DEFINE_KERNEL(S, true, threshold_pos)
+#define THR_DEFINE_WIDTH(S) THR_DEFINE_KERNEL(S, kFeedGrouped, threshold)
+#define THR_DEFINE_WIDTH_POS(S) THR_DEFINE_KERNEL(S, kFeedPos, threshold_pos)
 
 // The staged carry-save kernel of counter width S (thr_staged.cuh).
 #define THR_DEFINE_STAGED(S)                                                  \
