@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kNT, (S <= 6 ? 4 : (S <= 8 ? 3 : 2)))
         const uint32_t x0 = g * uint32_t(kGW);
         const uint32_t x1 = min(x0 + uint32_t(kGW), p.W);
         uint32_t k = 0, d = 0;
-        count_subtile<CsaCount<S>, false, false>(p, q, x0, x1, lane, ws, count, k, d);
+        count_subtile<CsaCount<S>, kFeedGrouped, false>(p, q, x0, x1, lane, ws, count, k, d);
         if (uint64_t(k) + d < L) continue;  // no row reaches the bound
         // valid rows of the lane's words (half h = 2 r + high word)
         uint32_t vm[8];
