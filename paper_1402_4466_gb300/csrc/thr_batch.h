@@ -77,10 +77,14 @@ thr_status autotune(const thr_index* idx, const BatchInput& in, cudaStream_t st,
                     double* times, uint32_t* best, bool share);
 
 // Counting variant per query for a thr_query_batch policy (thr_select.cu);
-// variant_flag: the THR_VARIANT_* of the flags (THR_POLICY_PLAIN).
+// variant_flag: the THR_VARIANT_* of the flags (THR_POLICY_PLAIN).  share:
+// queries over one id multiset will share a counting pass (no THR_NO_SHARE),
+// so under the RULE and LEARNED policies they keep the grouped carry-save
+// variant that shares.
 thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint32_t policy,
-                           uint32_t variant_flag, std::vector<uint8_t>* var);
+                           uint32_t variant_flag, std::vector<uint8_t>* var,
+                           bool share = true);
 thr_status learned_choice(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                           const uint32_t* ids, const uint32_t* T, std::vector<uint8_t>* var,
                           bool* used);

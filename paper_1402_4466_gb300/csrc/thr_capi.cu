@@ -197,7 +197,8 @@ static thr_status check_batch(const thr_index* idx, uint32_t nq, const uint32_t*
     for (uint64_t i = 0; i < id_off[nq]; ++i)
         if (ids[i] >= idx->nbitmaps)
             return fail(THR_E_INVAL, "id %u out of range (%u bitmaps)", ids[i], idx->nbitmaps);
-    return choose_variants(idx, nq, id_off, ids, T, policy, variant, cls);
+    return choose_variants(idx, nq, id_off, ids, T, policy, variant, cls,
+                           !(flags & THR_NO_SHARE));
 }
 
 extern "C" {

@@ -115,9 +115,40 @@ int variant_of_flag(uint32_t f) {
     }
 }
 
+// Queries of a batch over the same id multiset share one counting pass of
+// the grouped carry-save kernel (thr_batch.cu): the inputs are read and
+// counted once for all of them.  Both choosers price a query alone, so a
+// variant they predict faster for one member would cost the batch a second
+// pass over the same inputs; such members keep the default.  The multiset
+// key is order-independent (n and a sum of mixed ids); a collision only
+// keeps a query on the default, which is exact like every variant.
+void keep_shared_groups(uint32_t nq, const uint32_t* id_off, const uint32_t* ids,
+                        std::vector<uint8_t>* var) {
+    if (nq < 2) return;
+    std::vector<std::pair<uint64_t, uint32_t>> keys(nq);
+    for (uint32_t q = 0; q < nq; ++q) {
+        uint64_t h = 0;
+        for (uint32_t i = id_off[q]; i < id_off[q + 1]; ++i) {
+            uint64_t x = uint64_t(ids[i]) + 0x9E3779B97F4A7C15ull;  // splitmix64 of the id
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            h += x ^ (x >> 31);
+        }
+        keys[q] = {h ^ (uint64_t(id_off[q + 1] - id_off[q]) << 40), q};
+    }
+    std::sort(keys.begin(), keys.end());
+    for (uint32_t a = 0; a < nq;) {
+        uint32_t b = a + 1;
+        while (b < nq && keys[b].first == keys[a].first) ++b;
+        if (b - a > 1)
+            for (uint32_t k = a; k < b; ++k) (*var)[keys[k].second] = uint8_t(kVarCsa);
+        a = b;
+    }
+}
+
 thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id_off,
                            const uint32_t* ids, const uint32_t* T, uint32_t policy,
-                           uint32_t variant_flag, std::vector<uint8_t>* cls) {
+                           uint32_t variant_flag, std::vector<uint8_t>* cls, bool share) {
     cls->assign(nq, uint8_t(kVarCsa));
     if (policy == THR_POLICY_PLAIN) {
         const int v = variant_of_flag(variant_flag);
@@ -130,12 +161,14 @@ thr_status choose_variants(const thr_index* idx, uint32_t nq, const uint32_t* id
         if (s != THR_OK) return s;
         if (used) {
             drop_split_when_saturated(idx, nq, cls);
+            if (share) keep_shared_groups(nq, id_off, ids, cls);
             return THR_OK;
         }
     }
     for (uint32_t q = 0; q < nq; ++q)
         (*cls)[q] = rule_choice(idx, ids + id_off[q], id_off[q + 1] - id_off[q], T[q]);
     drop_split_when_saturated(idx, nq, cls);
+    if (share) keep_shared_groups(nq, id_off, ids, cls);
     return THR_OK;
 }
 
