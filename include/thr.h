@@ -252,7 +252,10 @@ thr_status thr_query_opt_batch(const thr_index *idx, uint32_t nq, const uint32_t
  *             with THR_OUT_DEVICE); query q's result is stored at
  *             pool[out_off[q] .. out_off[q] + out_len[q])
  *   out_off, out_len  host arrays of nq entries, filled on return
- *   flags     THR_OUT_DEVICE | one THR_POLICY_* value
+ *   flags     THR_OUT_DEVICE | one THR_POLICY_* value (RULE and LEARNED
+ *             choose a counting variant per query, except that queries
+ *             over the same id multiset keep THR_VARIANT_CSA, whose one
+ *             counting pass they share, unless THR_NO_SHARE is given)
  * pool_cap >= nq * (ceil(r/64) + 1) never yields THR_E_NOSPACE; a smaller
  * pool works when the results fit, else THR_E_NOSPACE with out_len holding
  * every query's length.  Results are identical to nq calls of thr_query.
